@@ -1,0 +1,366 @@
+"""Benchmark: batched QP forward+backward solves/s on a GB300.
+
+Workload (one "step"): 128 random dense QPs with n = 100 variables, 100 inequalities and
+50 equalities (Q = LLᵀ + 1e-3·I, G, A normal, h = G z0 + s0, b = A z0), FP32 factors with
+FP64-accurate residuals, forward (qp_forward) + backward (qp_backward with dℓ/dz* ~ N(0,1)),
+all inputs resident in HBM.  L2 is flushed (a 256 MiB write) between timed steps, outside
+the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own batch (instances rank·B .. rank·B+B−1; weak scaling,
+no data-path collective); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+B_DEFAULT, N_DEFAULT, NINEQ_DEFAULT, NEQ_DEFAULT = 128, 100, 100, 50
+METRIC = "QP fwd+bwd solves/sec (n=100, batch 128) @ rel err ≤1e-5; p50/p99 latency served"
+UNIT = "solves/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs × FP32 lanes × 2 flop/FMA × max clock
+
+
+def algorithmic_flops(n, p, m, iters):
+    """FLOPs (2 per FMA) of the block-eliminated method per solve: setup factorisations,
+    `iters` interior point iterations, the final factorisation and the backward solve."""
+    setup = (n ** 3 / 3 + n * n * (p + m) + m * m * n / 2 + m ** 3 / 3 + m * p * n
+             + p * p * n / 2 + m * m * p / 2 + p * p * m / 2)
+    per_iter = p ** 3 / 3 + 2 * (p * p + 2 * n * p + 2 * n * m + n * n)
+    final = p ** 3 / 3 + n * n
+    backward = (p * p + 2 * n * p + 2 * n * m + n * n) + n * n + n * p + n * m
+    fwd = 2 * (setup + iters * per_iter + final)
+    return fwd, 2 * backward
+
+
+def algorithmic_bytes(n, p, m, esz=4):
+    fwd_in = esz * (n * n + n * p + n * m + n + p + m)
+    fwd_out = esz * (n + p + m)
+    bwd = esz * n + fwd_in
+    return fwd_in + fwd_out + bwd
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(HERE, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def _oracle_instance(args):
+    """Forward + backward of one instance with the FP64 oracle (runs in a worker process)."""
+    n, p, m, idx = args
+    import oracle
+    from paper_1703_00443_gb300 import inputs
+    Q, q, G, h, A, b = inputs.random_qp(n, p, m, workload=inputs.WL_SWEEP, index=idx,
+                                        dtype=np.float32)
+    g = inputs.upstream_grad(1, n, workload=inputs.WL_SWEEP, start=idx)[0].astype(np.float64)
+    t0 = time.perf_counter()
+    sol = oracle.solve(Q, q, G, h, A, b)
+    gr = oracle.backward(Q, G, h, A, sol, g)
+    dt = time.perf_counter() - t0
+    return idx, dt, sol["z"], gr["dq"], gr["dG"], gr["dQ"]
+
+
+def _oracle_pool(workers):
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                            "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    pool = mp.get_context("spawn").Pool(workers)
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    return pool
+
+
+def cpu_baseline(n, p, m, budget_s=15.0, gpu_out=None):
+    """The oracle as it stands, one instance per process (BLAS threads = 1), all host cores,
+    on a bounded sample of the same instances; also returns its results for an accuracy
+    check of the GPU outputs on that sample."""
+    cores = os.cpu_count() or 1
+    pool = _oracle_pool(cores)
+    try:
+        pool.map(_oracle_instance, [(n, p, m, 0)] * cores)   # warm up the workers
+        t0 = time.perf_counter()
+        done = []
+        batch_idx = 0
+        while time.perf_counter() - t0 < budget_s and batch_idx * cores < B_DEFAULT:
+            idxs = [batch_idx * cores + k for k in range(cores)]
+            done += pool.map(_oracle_instance, [(n, p, m, i) for i in idxs if i < B_DEFAULT])
+            batch_idx += 1
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    res = {"value": len(done) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(done)} of the {B_DEFAULT} step instances (n={n}, nineq={p}, neq={m}), "
+                     f"FP64 dense-KKT PDIPM fwd+bwd, one instance per process, BLAS threads 1"}
+    acc = None
+    if gpu_out is not None and done:
+        ez, eg = [], []
+        for idx, _, z, dq, dG, dQ in done:
+            def rel(a, r):
+                return float(np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-12))
+            ez.append(rel(gpu_out["z"][idx], z))
+            eg.append(max(rel(gpu_out["dq"][idx], dq), rel(gpu_out["dG"][idx], dG),
+                          rel(gpu_out["dQ"][idx], dQ)))
+        acc = {"instances": len(done), "z_rel_err_max": max(ez), "grad_rel_err_max": max(eg)}
+    return res, acc
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    n, p, m = N_DEFAULT, NINEQ_DEFAULT, NEQ_DEFAULT
+    cores = os.cpu_count() or 1
+    pool = _oracle_pool(cores)
+    per_step = cores   # each step: one instance per core (a bounded sample of the batch)
+    try:
+        for w in range(args.warmup):
+            pool.map(_oracle_instance, [(n, p, m, k) for k in range(per_step)])
+        times = []
+        for s in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_instance, [(n, p, m, (s * per_step + k) % B_DEFAULT)
+                                        for k in range(per_step)])
+            times.append(time.perf_counter() - t0)
+    finally:
+        pool.close()
+        pool.join()
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"random dense QP fwd+bwd, n={n}, nineq={p}, neq={m}, batch {B_DEFAULT}",
+                       "n": n, "nineq": p, "neq": m, "batch": B_DEFAULT,
+                       "step": f"{per_step} instances of the batch per step (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} instances per step, one per process, BLAS threads 1"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward
+    from paper_1703_00443_gb300.qp import alloc_workspace
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B, n, p, m = args.batch, N_DEFAULT, NINEQ_DEFAULT, NEQ_DEFAULT
+    batch = inputs.random_batch(B, n, p, m, workload=inputs.WL_SWEEP, dtype=np.float32,
+                                start=rank * B)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP, start=rank * B)
+    host = [batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b, g]
+    dev_in = [torch.from_numpy(x).to(dev) for x in host]
+    Q, q, G, h, A, b, dl = dev_in
+    wsbuf = alloc_workspace(torch.float32, B, n, p, m, dev)
+    z = torch.empty((B, n), device=dev)
+    lam = torch.empty((B, p), device=dev)
+    nu = torch.empty((B, m), device=dev)
+    st = torch.empty((B,), device=dev, dtype=torch.int32)
+    it = torch.empty((B,), device=dev, dtype=torch.int32)
+    gout = [torch.empty(s, device=dev) for s in [(B, n, n), (B, n), (B, p, n), (B, p), (B, m, n), (B, m)]]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fwd = qp_forward(Q, q, G, h, A, b, workspace=wsbuf, out=(z, lam, nu, st, it))
+        qp_backward(fwd, dl, out=gout)
+        return fwd
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        fwd = qp_forward(Q, q, G, h, A, b, workspace=wsbuf, out=(z, lam, nu, st, it))
+        e1.record(stream)
+        qp_backward(fwd, dl, out=gout)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    fwd_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    bwd_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    step_ms = sum(fwd_ms) / args.steps + sum(bwd_ms) / args.steps
+
+    # End to end through the public API: pinned host inputs -> device, solve, read back
+    # z* and the six gradients each step.
+    pinned = [torch.from_numpy(x).pin_memory() for x in host]
+    outs_h = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in [z] + gout]
+    h2d = sum(t.numel() * t.element_size() for t in pinned)
+    d2h = sum(t.numel() * t.element_size() for t in outs_h)
+    e2e_ms = []
+    for k in range(args.steps + 2):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, hsrc in zip(dev_in, pinned):
+            d.copy_(hsrc, non_blocking=True)
+        fwd = qp_forward(Q, q, G, h, A, b, workspace=wsbuf, out=(z, lam, nu, st, it))
+        qp_backward(fwd, dl, out=gout)
+        for hdst, d in zip(outs_h, [z] + gout):
+            hdst.copy_(d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            e2e_ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+
+    # Max over ranks.
+    tvec = torch.tensor([step_ms, sum(fwd_ms) / args.steps, statistics.mean(e2e_ms)], device=dev,
+                        dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(tvec, op=dist.ReduceOp.MAX)
+    step_ms, fwd_mean, e2e_mean = tvec.tolist()
+    status = st.cpu().numpy()
+    iters = it.cpu().numpy()
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    value = ws * B / (step_ms / 1e3)
+    e2e_value = ws * B / (e2e_mean / 1e3)
+    k_mean = float(iters.mean())
+    f_fwd, f_bwd = algorithmic_flops(n, p, m, k_mean)
+    achieved = f_fwd * B / (fwd_mean / 1e3) / 1e12
+    gpu_out = {"z": z.cpu().numpy(), "dq": gout[1].cpu().numpy(), "dG": gout[2].cpu().numpy(),
+               "dQ": gout[0].cpu().numpy()}
+    cpu, acc = (None, None)
+    if not args.no_cpu_baseline and ws == 1:
+        cpu, acc = cpu_baseline(n, p, m, budget_s=args.cpu_budget, gpu_out=gpu_out)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random QPs, recipe of the paper's timing experiment)",
+        "config": {"workload": f"random dense QP fwd+bwd, n={n}, nineq={p}, neq={m}, batch {B}",
+                   "n": n, "nineq": p, "neq": m, "batch": B, "per_gpu_batch": B,
+                   "precision": "FP32 factors, FP64-accurate residual/iterate/refinement",
+                   "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "parallelism": f"independent batches per GPU x{ws}",
+                   "fwd_ms": fwd_mean, "bwd_ms": step_ms - fwd_mean,
+                   "iters_mean": k_mean, "iters_max": int(iters.max()),
+                   "status_counts": {str(s): int((status == s).sum()) for s in np.unique(status)},
+                   "wall_s_timed_loop": t_wall},
+        "roofline": {"bound": "alu", "kernel": "qp_fwd_kernel", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "traffic": None,
+                     "algorithmic_flops_per_launch": f_fwd * B},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "accuracy_vs_oracle": acc,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=B_DEFAULT)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,114 @@
+/*
+ * qp_gb300.h -- C ABI of the batched differentiable QP solver (OptNet hot path) for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Amos & Kolter 2017, §3, Eq. 2), one per batch instance:
+ *
+ *     minimise_z  ½ zᵀ Q z + qᵀ z   subject to   A z = b,  G z ≤ h
+ *
+ * with z ∈ Rⁿ, G ∈ R^{nineq×n}, A ∈ R^{neq×n}.  The paper writes A with m rows and G with
+ * p rows; this ABI names the row counts `nineq` (rows of G) and `neq` (rows of A).
+ *
+ * Layout: every matrix and vector argument is a DEVICE pointer to dense, row-major,
+ * batch-major data (instance b of Q starts at Q + b·n·n, of G at G + b·nineq·n, ...),
+ * of the element type chosen by `dtype`.  Q must be symmetric positive definite.
+ * Pointers must be aligned to the element size.  All calls are asynchronous on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and never synchronise the host.
+ *
+ * Ownership: the library never allocates device memory in these calls.  The caller owns
+ * every buffer, including the workspace that carries the factorisation from
+ * qp_forward to qp_backward (size from qp_workspace_bytes).
+ *
+ * Errors: call-level problems return a QP_E* code and launch nothing.  Per-instance
+ * numerical outcomes are reported in status[b] (QP_STATUS_*); kernels never trap.
+ */
+#ifndef QP_GB300_H
+#define QP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define QP_OK            0
+#define QP_EINVAL        1  /* null pointer, negative size, bad dtype, B = 0 allowed */
+#define QP_ENOSPACE      2  /* workspace smaller than qp_workspace_bytes()          */
+#define QP_EUNSUPPORTED  3  /* sizes beyond what the kernels of this build handle   */
+#define QP_ECUDA         4  /* a CUDA launch or attribute call failed               */
+
+/* Element types. */
+#define QP_F32 0  /* FP32 matrices and factors; FP64-accurate residuals and iterate */
+#define QP_F64 1  /* everything in FP64                                              */
+
+/* Per-instance status codes written to status[b]. */
+#define QP_STATUS_CONVERGED 0  /* residual and duality tests met                          */
+#define QP_STATUS_MAX_ITER  1  /* max_iter Newton steps taken; iterate returned anyway   */
+#define QP_STATUS_NOT_PD    2  /* a pivot of Q, of A Q⁻¹Aᵀ or of the per-iteration Schur
+                                  complement was not positive: outputs are NaN          */
+#define QP_STATUS_NUMERICAL 3  /* a non-finite value appeared: outputs are NaN           */
+
+typedef struct qp_options {
+  double  tol;       /* stop when ‖r_z‖∞ ≤ tol·(1+‖q‖∞), ‖Gz+s−h‖∞ ≤ tol·(1+‖h‖∞),
+                        ‖Az−b‖∞ ≤ tol·(1+‖b‖∞) ...                                   */
+  double  mu_tol;    /* ... and μ = sᵀλ/nineq ≤ mu_tol                                */
+  int32_t max_iter;  /* bound on Newton steps of the interior point loop               */
+  int32_t refine;    /* FP64 iterative-refinement steps of the backward KKT solve (0-2) */
+} qp_options;
+
+/* Default options for a dtype (QP_F32: tol 1e-10, mu_tol 1e-11, max_iter 50, refine 1;
+ * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 1). */
+void qp_default_options(int dtype, qp_options* opt);
+
+/* Bytes of workspace qp_forward needs for B instances of one size (0 on invalid sizes). */
+size_t qp_workspace_bytes(int dtype, int B, int n, int nineq, int neq);
+
+/* QP_OK if this build's kernels handle the size, else QP_EUNSUPPORTED / QP_EINVAL. */
+int qp_supported(int dtype, int n, int nineq, int neq);
+
+/*
+ * qp_forward -- batched primal-dual interior point solve (§3.1: slack form, affine
+ * predictor Eq. 9, centering-plus-corrector Eq. 10, symmetrised and block-eliminated KKT
+ * system with the parts that do not involve D(λ/s) factored once).
+ *
+ * In:   Q [B,n,n], q [B,n], G [B,nineq,n], h [B,nineq], A [B,neq,n], b [B,neq].
+ *       G/h may be NULL when nineq = 0, A/b may be NULL when neq = 0.
+ * Out:  z [B,n] = z*, lam [B,nineq] = λ*, nu [B,neq] = ν* (lam/nu may be NULL when their
+ *       size is 0), status [B] (QP_STATUS_*), iters [B] (Newton steps taken).
+ * Work: workspace of at least qp_workspace_bytes(dtype,B,n,nineq,neq) bytes, 256-byte
+ *       aligned; it keeps the factorisation at the returned iterate and the FP64 iterate
+ *       for qp_backward.  It must not be modified between the two calls.
+ * opt:  NULL = qp_default_options(dtype).
+ */
+int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+               const void* Q, const void* q, const void* G, const void* h,
+               const void* A, const void* b,
+               void* z, void* lam, void* nu, int32_t* status, int32_t* iters,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * qp_backward -- gradients of ℓ(z*) through the KKT conditions (§3, Eq. 7 and Eq. 8),
+ * computed as in §3.1.1 (Eq. 11) with the factorisation qp_forward left in `workspace`:
+ * K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z*; 0; 0; 0], then
+ *   dQ = ½(d_z z*ᵀ + z* d_zᵀ), dq = d_z, dG = d̃_λ z*ᵀ + λ* d_zᵀ, dh = −d̃_λ,
+ *   dA = d_ν z*ᵀ + ν* d_zᵀ,    db = −d_ν.
+ * `refine` steps of iterative refinement with an FP64-accurate KKT residual follow the
+ * first solve.  Q, G, A must be the same data passed to qp_forward (they feed the
+ * refinement residual).  dl_dz [B,n] is ∂ℓ/∂z*.  Any gradient pointer may be NULL
+ * (not wanted).  Instances whose forward status was NOT_PD or NUMERICAL get NaN
+ * gradients.
+ */
+int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+                const void* Q, const void* G, const void* A,
+                const void* workspace, size_t workspace_bytes, const void* dl_dz,
+                void* dQ, void* dq, void* dG, void* dh, void* dA, void* db, void* stream);
+
+/* Human-readable text for a QP_E* code. */
+const char* qp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QP_GB300_H */

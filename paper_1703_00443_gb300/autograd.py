@@ -1,0 +1,41 @@
+"""``QPFunction``: the OptNet QP layer as a ``torch.autograd.Function`` (§3).
+
+forward(Q, q, G, h, A, b) -> z* (λ* and ν* are returned too, marked non-differentiable:
+the paper forms Jacobians of z* only).  backward(∂ℓ/∂z*) -> the six parameter gradients of
+Eq. 8, from the factorisation the forward pass left in its workspace (§3.1.1).
+"""
+from __future__ import annotations
+
+import torch
+
+from .qp import qp_backward, qp_forward
+
+
+class QPFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Q, q, G, h, A, b, options=None):
+        fwd = qp_forward(Q, q, G, h, A, b, options=options)
+        ctx.fwd = fwd
+        ctx.shapes = (G is None, A is None)
+        ctx.mark_non_differentiable(fwd.lam, fwd.nu, fwd.status)
+        return fwd.z, fwd.lam, fwd.nu, fwd.status
+
+    @staticmethod
+    def backward(ctx, dz, dlam, dnu, dstatus):
+        if dz is None:
+            return (None,) * 7
+        need = ctx.needs_input_grad[:6]
+        g = qp_backward(ctx.fwd, dz, need=tuple(bool(x) for x in need))
+        no_g, no_a = ctx.shapes
+        grads = list(g)
+        if no_g:
+            grads[2] = grads[3] = None
+        if no_a:
+            grads[4] = grads[5] = None
+        return (*grads, None)
+
+
+def qp_layer(Q, q, G=None, h=None, A=None, b=None, options=None):
+    """z* of the batch, differentiable with respect to every input tensor."""
+    z, _, _, _ = QPFunction.apply(Q, q, G, h, A, b, options)
+    return z

@@ -1,0 +1,205 @@
+// qp_abi.cu -- the C ABI declared in include/qp_gb300.h: argument checks, kernel-variant
+// choice and launches.  No device memory is allocated here; the caller owns every buffer.
+#include <stdint.h>
+
+#include "qp_gb300.h"
+#include "qp_launch.cuh"
+
+namespace {
+
+constexpr int kDefaultSmemOptin = 232448;  // 227 KiB, used when no device is visible
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return kDefaultSmemOptin;
+  }
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return kDefaultSmemOptin;
+  }
+  return v;
+}
+
+bool dims_ok(int B, int n, int nineq, int neq) {
+  return B >= 0 && n >= 1 && nineq >= 0 && neq >= 0 && neq <= n;
+}
+
+int tiles_of(int N) {
+  const int NT = (N + 3) / 4;
+  return NT * (NT + 1) / 2;
+}
+
+// Smallest compiled (SW, CH) variant whose register tiles cover the sweep matrix of order
+// n + neq + nineq and the nineq×nineq Schur complement.
+bool pick_variant(int dtype, int n, int nineq, int neq, int* SW, int* CH) {
+  const int t3 = tiles_of(n + neq + nineq), tp = tiles_of(nineq);
+  const int sws[3] = {1, 2, 4};
+  const int esz = dtype == QP_F32 ? 4 : 8;
+  for (int ch = 1; ch <= 2; ++ch) {
+    if (ch * qpk::NTHREADS < tp) continue;
+    for (int i = 0; i < 3; ++i) {
+      const int sw = sws[i];
+      if (sw * qpk::NTHREADS < t3) continue;
+      if (!qpk::fwd_variant_exists(esz, sw, ch)) continue;
+      *SW = sw;
+      *CH = ch;
+      return true;
+    }
+  }
+  return false;
+}
+
+size_t fwd_smem(int dtype, int n, int nineq, int neq) {
+  if (dtype == QP_F32) {
+    qpk::FwdSmem<float> L;
+    L.init(n, nineq, neq);
+    return L.total;
+  }
+  qpk::FwdSmem<double> L;
+  L.init(n, nineq, neq);
+  return L.total;
+}
+
+size_t bwd_smem(int dtype, int n, int nineq, int neq) {
+  if (dtype == QP_F32) {
+    qpk::BwdSmem<float> L;
+    L.init(n, nineq, neq);
+    return L.total;
+  }
+  qpk::BwdSmem<double> L;
+  L.init(n, nineq, neq);
+  return L.total;
+}
+
+size_t ws_inst(int dtype, int n, int nineq, int neq) {
+  qpk::WsLayout W;
+  W.init(n, nineq, neq, dtype == QP_F32 ? 4 : 8);
+  return W.inst;
+}
+
+}  // namespace
+
+namespace qpk {
+bool fwd_variant_exists(int esz, int SW, int CH) {
+  if (esz == 4) return (CH == 1 && (SW == 1 || SW == 2 || SW == 4)) || (CH == 2 && SW == 4);
+  return CH == 1 && (SW == 1 || SW == 2);
+}
+}  // namespace qpk
+
+extern "C" {
+
+void qp_default_options(int dtype, qp_options* opt) {
+  if (!opt) return;
+  if (dtype == QP_F64) {
+    opt->tol = 1e-12;
+    opt->mu_tol = 1e-13;
+    opt->max_iter = 100;
+  } else {
+    opt->tol = 1e-10;
+    opt->mu_tol = 1e-11;
+    opt->max_iter = 50;
+  }
+  opt->refine = 1;
+}
+
+size_t qp_workspace_bytes(int dtype, int B, int n, int nineq, int neq) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return 0;
+  return (size_t)B * ws_inst(dtype, n, nineq, neq);
+}
+
+int qp_supported(int dtype, int n, int nineq, int neq) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(1, n, nineq, neq)) return QP_EINVAL;
+  int sw, ch;
+  if (!pick_variant(dtype, n, nineq, neq, &sw, &ch)) return QP_EUNSUPPORTED;
+  if (fwd_smem(dtype, n, nineq, neq) > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
+  if (bwd_smem(dtype, n, nineq, neq) > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
+  return QP_OK;
+}
+
+int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+               const void* Q, const void* q, const void* G, const void* h, const void* A,
+               const void* b, void* z, void* lam, void* nu, int32_t* status, int32_t* iters,
+               void* workspace, size_t workspace_bytes, void* stream) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return QP_EINVAL;
+  if (B == 0) return QP_OK;
+  if (!Q || !q || !z || !workspace) return QP_EINVAL;
+  if (nineq > 0 && (!G || !h)) return QP_EINVAL;
+  if (neq > 0 && (!A || !b)) return QP_EINVAL;
+  if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
+  if (workspace_bytes < qp_workspace_bytes(dtype, B, n, nineq, neq)) return QP_ENOSPACE;
+  int sw = 0, ch = 0;
+  if (!pick_variant(dtype, n, nineq, neq, &sw, &ch)) return QP_EUNSUPPORTED;
+  const size_t smem = fwd_smem(dtype, n, nineq, neq);
+  if (smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
+  qp_options o;
+  if (opt) o = *opt; else qp_default_options(dtype, &o);
+  if (o.max_iter < 0) return QP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (dtype == QP_F32) {
+    qpk::FwdParams<float> P{B, n, nineq, neq,
+                            (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
+                            (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
+                            status, iters, (unsigned char*)workspace,
+                            ws_inst(dtype, n, nineq, neq), o.tol, o.mu_tol, o.max_iter};
+    e = qpk::launch_fwd_f32(P, sw, ch, smem, st);
+  } else {
+    qpk::FwdParams<double> P{B, n, nineq, neq,
+                             (const double*)Q, (const double*)q, (const double*)G, (const double*)h,
+                             (const double*)A, (const double*)b, (double*)z, (double*)lam,
+                             (double*)nu, status, iters, (unsigned char*)workspace,
+                             ws_inst(dtype, n, nineq, neq), o.tol, o.mu_tol, o.max_iter};
+    e = qpk::launch_fwd_f64(P, sw, ch, smem, st);
+  }
+  return e == cudaSuccess ? QP_OK : QP_ECUDA;
+}
+
+int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+                const void* Q, const void* G, const void* A, const void* workspace,
+                size_t workspace_bytes, const void* dl_dz, void* dQ, void* dq, void* dG,
+                void* dh, void* dA, void* db, void* stream) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return QP_EINVAL;
+  if (B == 0) return QP_OK;
+  if (!Q || !dl_dz || !workspace) return QP_EINVAL;
+  if (nineq > 0 && !G) return QP_EINVAL;
+  if (neq > 0 && !A) return QP_EINVAL;
+  if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
+  if (workspace_bytes < qp_workspace_bytes(dtype, B, n, nineq, neq)) return QP_ENOSPACE;
+  const size_t smem = bwd_smem(dtype, n, nineq, neq);
+  if (smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
+  qp_options o;
+  if (opt) o = *opt; else qp_default_options(dtype, &o);
+  if (o.refine < 0 || o.refine > 4) return QP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (dtype == QP_F32) {
+    qpk::BwdParams<float> P{B, n, nineq, neq, (const float*)Q, (const float*)G, (const float*)A,
+                            (const float*)dl_dz, (float*)dQ, (float*)dq, (float*)dG, (float*)dh,
+                            (float*)dA, (float*)db, (const unsigned char*)workspace,
+                            ws_inst(dtype, n, nineq, neq), o.refine};
+    e = qpk::launch_bwd_f32(P, smem, st);
+  } else {
+    qpk::BwdParams<double> P{B, n, nineq, neq, (const double*)Q, (const double*)G,
+                             (const double*)A, (const double*)dl_dz, (double*)dQ, (double*)dq,
+                             (double*)dG, (double*)dh, (double*)dA, (double*)db,
+                             (const unsigned char*)workspace, ws_inst(dtype, n, nineq, neq),
+                             o.refine};
+    e = qpk::launch_bwd_f64(P, smem, st);
+  }
+  return e == cudaSuccess ? QP_OK : QP_ECUDA;
+}
+
+const char* qp_strerror(int code) {
+  switch (code) {
+    case QP_OK: return "ok";
+    case QP_EINVAL: return "invalid argument (dtype, sizes, null or misaligned pointer)";
+    case QP_ENOSPACE: return "workspace smaller than qp_workspace_bytes()";
+    case QP_EUNSUPPORTED: return "problem size beyond what the compiled kernels handle";
+    case QP_ECUDA: return "CUDA launch or attribute call failed";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,955 @@
+// qp_device.cuh -- device code of the batched differentiable QP solver for sm_103a.
+//
+// One thread block (512 threads) owns one QP instance for the whole solve, so the
+// interior point loop runs without a host round trip and each instance stops on its own
+// convergence test.  Method: Amos & Kolter 2017, §3.1 (Mehrotra predictor-corrector
+// primal-dual interior point method in slack form, Eq. 9 and Eq. 10, with the KKT system
+// symmetrised and block-eliminated so that only an nineq×nineq matrix is factored per
+// iteration) and §3.1.1 (backward pass with the factorisation at the solution, Eq. 11).
+//
+// Block elimination used here.  With K11 = [Q Aᵀ; A 0] (the part of the symmetrised KKT
+// matrix that never changes) and S = K11⁻¹ = [P T; Tᵀ −S_A⁻¹], the Newton system
+//     [Q Gᵀ Aᵀ; G −D(s/λ) 0; A 0 0] [Δz; Δλ; Δν] = [r1; r̃3; r4]
+// reduces to
+//     (M + D(s/λ)) Δλ = RE·[r1; r4] − r̃3,   [Δz; Δν] = S·[r1; r4] − REᵀ Δλ,
+// where RE = [G 0]·S = [GP, GT] (nineq × (n+neq)) and M = G P Gᵀ.  S, RE and M are
+// produced together, once per solve, by a symmetric Gauss-Jordan sweep over the first
+// n+neq pivots of [[K11, [G 0]ᵀ], [[G 0], 0]] held in registers (4×4 tiles per thread).
+// Each iteration factors M + D(s/λ) = L Lᵀ by a right-looking Cholesky that also forms
+// X = L⁻¹ in the same column loop, so every triangular solve is a product with X or Xᵀ.
+//
+// Precision.  T is the matrix/factor type (float or double).  The iterate (z, s, λ, ν)
+// is kept in FP64, and the KKT residual, the convergence test, the step lengths and the
+// backward refinement residual are FP64-accurate.  For T = float the residual products
+// use error-free FP32 transformations (Dekker's product by FMA and Knuth's two-sum), a
+// double-float accumulation whose error is about 2⁻⁴⁸ of Σ|terms|, because the FP64 pipe
+// of this part is a small fraction of the FP32 rate.  The Newton directions themselves
+// are FP32; with an exact residual each iteration acts as a refinement step, so the
+// returned iterate is accurate well past FP32 precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace qpk {
+
+constexpr int NTHREADS = 512;
+constexpr int NWARPS = NTHREADS / 32;
+
+enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3 };
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ layouts
+// Per-instance workspace (global memory) kept from forward to backward.
+struct WsLayout {
+  size_t oSR, oX, oIt, oSt, inst;
+  __host__ __device__ void init(int n, int p, int m, int esz) {
+    const size_t m1 = (size_t)n + m;
+    oSR = 0;
+    oX = align_up(oSR + (m1 + p) * m1 * esz, 256);
+    oIt = align_up(oX + (size_t)p * p * esz, 256);
+    oSt = align_up(oIt + 8 * ((size_t)n + 2 * (size_t)p + m), 256);
+    inst = align_up(oSt + 16, 256);
+  }
+};
+
+// Dynamic shared memory of the forward kernel.
+template <typename T>
+struct FwdSmem {
+  int m1, N3, ldS, ldM, NT3, NTp;
+  size_t oSR, oMb, odM, ocb, odbl, osplit, ovec, ored, oscr, total;
+  __host__ __device__ void init(int n, int p, int m) {
+    m1 = n + m;
+    N3 = m1 + p;
+    ldS = m1;
+    ldM = p > 0 ? p : 1;
+    NT3 = (N3 + 3) / 4;
+    NTp = (p + 3) / 4;
+    const size_t es = sizeof(T);
+    size_t o = 0;
+    oSR = o;   o = align_up(o + (size_t)(m1 + p) * ldS * es, 16);
+    oMb = o;   o = align_up(o + (size_t)p * ldM * es, 16);
+    odM = o;   o = align_up(o + (size_t)p * es, 16);
+    ocb = o;
+    {
+      size_t a = 2 * 4 * (size_t)NT3, b = 2 * 8 * (size_t)NTp;
+      o = align_up(o + (a > b ? a : b) * es, 16);
+    }
+    odbl = o;  o = align_up(o + 8 * (2 * (size_t)n + 5 * (size_t)p + 2 * (size_t)m), 16);
+    osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
+    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 8 * (size_t)p), 16);
+    ored = o;  o = align_up(o + 8 * 4 * NWARPS, 16);
+    oscr = o;  o = align_up(o + 8 * (size_t)NTHREADS, 16);
+    total = o;
+  }
+};
+
+// Dynamic shared memory of the backward kernel (vectors only).
+template <typename T>
+struct BwdSmem {
+  size_t odbl, osplit, ovec, ored, oscr, total;
+  __host__ __device__ void init(int n, int p, int m) {
+    const size_t m1 = (size_t)n + m, es = sizeof(T);
+    size_t o = 0;
+    odbl = o;   o = align_up(o + 8 * (3 * ((size_t)n + p + m) + 2 * (size_t)p), 16);
+    osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
+    ovec = o;   o = align_up(o + es * (3 * m1 + 4 * (size_t)p), 16);
+    ored = o;   o = align_up(o + 8 * 4 * NWARPS, 16);
+    oscr = o;   o = align_up(o + 8 * (size_t)NTHREADS, 16);
+    total = o;
+  }
+};
+
+template <typename T>
+struct FwdParams {
+  int B, n, p, m;
+  const T *Q, *q, *G, *h, *A, *b;
+  T *z, *lam, *nu;
+  int32_t *status, *iters;
+  unsigned char* ws;
+  size_t ws_inst;
+  double tol, mu_tol;
+  int max_iter;
+};
+
+template <typename T>
+struct BwdParams {
+  int B, n, p, m;
+  const T *Q, *G, *A, *dl_dz;
+  T *dQ, *dq, *dG, *dh, *dA, *db;
+  const unsigned char* ws;
+  size_t ws_inst;
+  int refine;
+};
+
+// ------------------------------------------------------------------ FP64-accurate dot products
+template <typename T> struct Split;
+template <> struct Split<float> {
+  using V = float2;
+  __device__ static __forceinline__ V make(double x) {
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+};
+template <> struct Split<double> {
+  using V = double;
+  __device__ static __forceinline__ V make(double x) { return x; }
+};
+
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+// Double-float accumulator: a·x_hi is split exactly into p + e (FMA), p is added to hi
+// with Knuth's two-sum, and all low-order parts go to lo.  __fadd_rn/__fmul_rn are never
+// contracted into FMAs, which keeps the transformations error-free.
+template <> struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float2 x) {
+    const float p = __fmul_rn(a, x.x);
+    const float e = fmaf(a, x.x, -p);
+    const float t = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, fmaf(a, x.y, e)));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ------------------------------------------------------------------ block reductions
+enum : int { R_SUM = 0, R_MAX = 1, R_MIN = 2 };
+
+template <int OP>
+__device__ __forceinline__ double rop(double a, double b) {
+  if (OP == R_SUM) return a + b;
+  if (OP == R_MAX) return (a > b || a != a) ? a : b;   // propagates NaN
+  return (a < b || a != a) ? a : b;
+}
+
+template <int O0, int O1, int O2, int O3>
+__device__ __forceinline__ void block_reduce4(double (&v)[4], double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v[0] = rop<O0>(v[0], __shfl_xor_sync(0xffffffffu, v[0], off));
+    v[1] = rop<O1>(v[1], __shfl_xor_sync(0xffffffffu, v[1], off));
+    v[2] = rop<O2>(v[2], __shfl_xor_sync(0xffffffffu, v[2], off));
+    v[3] = rop<O3>(v[3], __shfl_xor_sync(0xffffffffu, v[3], off));
+  }
+  if (lane == 0) {
+    red[4 * w + 0] = v[0];
+    red[4 * w + 1] = v[1];
+    red[4 * w + 2] = v[2];
+    red[4 * w + 3] = v[3];
+  }
+  __syncthreads();
+  double r0 = red[0], r1 = red[1], r2 = red[2], r3 = red[3];
+#pragma unroll
+  for (int i = 1; i < NWARPS; ++i) {
+    r0 = rop<O0>(r0, red[4 * i + 0]);
+    r1 = rop<O1>(r1, red[4 * i + 1]);
+    r2 = rop<O2>(r2, red[4 * i + 2]);
+    r3 = rop<O3>(r3, red[4 * i + 3]);
+  }
+  v[0] = r0; v[1] = r1; v[2] = r2; v[3] = r3;
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ matrix-vector products
+// y_r = Σ_c M[r·ld + c]·x[c] for r < rows (c ≤ r when `lower`), GL lanes per row.
+// Calls epi(r, y_r) once per row; the caller synchronises before reading the results.
+template <int GL, typename T, typename F>
+__device__ __forceinline__ void mv_rows(const T* M, int ld, int rows, int cols, bool lower,
+                                        const T* x, F epi) {
+  const int tid = threadIdx.x;
+  const int g = tid / GL, gl = tid % GL;
+  constexpr int NG = NTHREADS / GL;
+  for (int r0 = 0; r0 < rows; r0 += NG) {
+    const int r = r0 + g;
+    T acc0 = T(0), acc1 = T(0);
+    if (r < rows) {
+      const int cend = lower ? min(cols, r + 1) : cols;
+      const T* row = M + (size_t)r * ld;
+      int c = gl;
+      for (; c + GL < cend; c += 2 * GL) {
+        acc0 = fma(row[c], x[c], acc0);
+        acc1 = fma(row[c + GL], x[c + GL], acc1);
+      }
+      if (c < cend) acc0 = fma(row[c], x[c], acc0);
+    }
+    T acc = acc0 + acc1;
+#pragma unroll
+    for (int off = GL / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (r < rows && gl == 0) epi(r, acc);
+  }
+}
+
+// y_c = Σ_r M[r·ld + c]·x[r] for c < cols (r ≥ c when `lower`).  Row ranges are split over
+// the threads that share a column; partial sums meet in `scr` (NTHREADS entries).
+// Ends with a barrier, so epi's writes are visible on return.
+template <typename T, typename F>
+__device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, bool lower,
+                                        const T* x, T* scr, F epi) {
+  const int tid = threadIdx.x;
+  if (cols <= 0) return;
+  if (cols > NTHREADS / 2) {
+    for (int c = tid; c < cols; c += NTHREADS) {
+      T a0 = T(0), a1 = T(0);
+      int r = lower ? c : 0;
+      for (; r + 1 < rows; r += 2) {
+        a0 = fma(M[(size_t)r * ld + c], x[r], a0);
+        a1 = fma(M[(size_t)(r + 1) * ld + c], x[r + 1], a1);
+      }
+      if (r < rows) a0 = fma(M[(size_t)r * ld + c], x[r], a0);
+      epi(c, a0 + a1);
+    }
+    __syncthreads();
+    return;
+  }
+  const int nparts = NTHREADS / cols;
+  const int c = tid % cols, part = tid / cols;
+  if (part < nparts) {
+    const int chunk = (rows + nparts - 1) / nparts;
+    int r = part * chunk;
+    const int r1 = min(rows, r + chunk);
+    if (lower && r < c) r = c;
+    T a0 = T(0), a1 = T(0);
+    for (; r + 1 < r1; r += 2) {
+      a0 = fma(M[(size_t)r * ld + c], x[r], a0);
+      a1 = fma(M[(size_t)(r + 1) * ld + c], x[r + 1], a1);
+    }
+    if (r < r1) a0 = fma(M[(size_t)r * ld + c], x[r], a0);
+    scr[part * cols + c] = a0 + a1;
+  }
+  __syncthreads();
+  if (tid < cols) {
+    T s = T(0);
+    for (int q = 0; q < nparts; ++q) s += scr[q * cols + tid];
+    epi(tid, s);
+  }
+  __syncthreads();
+}
+
+// FP64-accurate application of the (unreduced, slack-eliminated) KKT operator:
+//   out_z = Q x_z + Gᵀ x_λ + Aᵀ x_ν + add_z,  out_λ = G x_z + add_λ,  out_ν = A x_z + add_ν.
+// x = [x_z; x_λ; x_ν] is given split (FP32 hi/lo pairs for T = float).  Q is symmetric, so
+// Q x_z is formed column-wise together with Gᵀx_λ and Aᵀx_ν from one pass over the rows of
+// [Q; G; A].  Ends with a barrier.
+template <typename T, typename FZ, typename FL, typename FN>
+__device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* Q, const T* G,
+                                          const T* A, const typename Split<T>::V* xv,
+                                          double* scr, FZ add_z, FL add_l, FN add_n,
+                                          double* out_z, double* out_l, double* out_n) {
+  const int tid = threadIdx.x;
+  const int R = n + p + m;
+  const bool split_rows = (n <= NTHREADS / 2);
+  const int nparts = split_rows ? NTHREADS / n : 1;
+  if (split_rows) {
+    const int j = tid % n, part = tid / n;
+    if (part < nparts) {
+      const int chunk = (R + nparts - 1) / nparts;
+      const int r0 = part * chunk, r1 = min(R, r0 + chunk);
+      Acc<T> acc;
+      for (int r = r0, e = min(r1, n); r < e; ++r) acc.add(Q[(size_t)r * n + j], xv[r]);
+      for (int r = max(r0, n), e = min(r1, n + p); r < e; ++r)
+        acc.add(G[(size_t)(r - n) * n + j], xv[r]);
+      for (int r = max(r0, n + p); r < r1; ++r) acc.add(A[(size_t)(r - n - p) * n + j], xv[r]);
+      scr[part * n + j] = acc.value();
+    }
+  } else {
+    for (int j = tid; j < n; j += NTHREADS) {
+      Acc<T> acc;
+      for (int r = 0; r < n; ++r) acc.add(Q[(size_t)r * n + j], xv[r]);
+      for (int r = 0; r < p; ++r) acc.add(G[(size_t)r * n + j], xv[n + r]);
+      for (int r = 0; r < m; ++r) acc.add(A[(size_t)r * n + j], xv[n + p + r]);
+      out_z[j] = acc.value() + add_z(j);
+    }
+  }
+  {
+    constexpr int GL = 8, NG = NTHREADS / GL;
+    const int g = tid / GL, gl = tid % GL;
+    for (int r0 = 0; r0 < p + m; r0 += NG) {
+      const int r = r0 + g;
+      double v = 0.0;
+      if (r < p + m) {
+        const T* row = (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
+        Acc<T> acc;
+        for (int c = gl; c < n; c += GL) acc.add(row[c], xv[c]);
+        v = acc.value();
+      }
+#pragma unroll
+      for (int off = GL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (r < p + m && gl == 0) {
+        if (r < p) out_l[r] = v + add_l(r);
+        else out_n[r - p] = v + add_n(r - p);
+      }
+    }
+  }
+  __syncthreads();
+  if (split_rows && tid < n) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += scr[q * n + tid];
+    out_z[tid] = s + add_z(tid);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ register tiles
+// Lower-triangular tiling of an N×N symmetric matrix by 4×4 tiles; linear tile t maps to
+// tile row I = ⌊(√(8t+1) − 1)/2⌋ and tile column J = t − I(I+1)/2.
+__device__ __forceinline__ void tile_of(int t, int& I, int& J) {
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  I = i;
+  J = t - i * (i + 1) / 2;
+}
+
+template <typename T>
+__device__ __forceinline__ T sel4(T a0, T a1, T a2, T a3, int k) {
+  return k == 0 ? a0 : (k == 1 ? a1 : (k == 2 ? a2 : a3));
+}
+
+// Element (i, j) of the symmetric matrix [[Q, Aᵀ, Gᵀ], [A, 0, 0], [G, 0, 0]] whose first
+// m1 = n + neq pivots are swept (rows ordered z, ν, λ).  Zero outside N×N.
+template <typename T>
+__device__ __forceinline__ T k3_elem(int n, int m1, int N, const T* Q, const T* A, const T* G,
+                                     int i, int j) {
+  if (i >= N || j >= N) return T(0);
+  if (i < j) { const int t = i; i = j; j = t; }
+  if (i < n) return Q[(size_t)i * n + j];
+  if (j >= n) return T(0);
+  if (i < m1) return A[(size_t)(i - n) * n + j];
+  return G[(size_t)(i - m1) * n + j];
+}
+
+// Symmetric Gauss-Jordan sweep (pivots 0 .. m1−1) of the matrix above, held in registers.
+// SWEEP(k): d = a_kk; a_kk ← −1/d; a_ik ← a_ik/d (i ≠ k); a_ij ← a_ij − a_ik a_kj / d.
+// Afterwards the top-left block is −K11⁻¹ = −S, the bottom-left block is RE = [G 0]·S and
+// the bottom-right block is −M.  Writes S and RE to SR (rows 0..m1−1 = S, m1.. = RE,
+// leading dimension ldS), M's strict upper triangle to Mb and diag(M) to dM.
+// The pivots must be positive for k < n (Q ≻ 0) and negative for k ≥ n (A of full row
+// rank); otherwise every thread returns false.
+template <typename T, int SW>
+__device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restrict__ Q,
+                                         const T* __restrict__ A, const T* __restrict__ G,
+                                         T* SR, int ldS, T* Mb, int ldM, T* dM, T* cb) {
+  const int tid = threadIdx.x;
+  const int m1 = n + m, N = m1 + p, NT = (N + 3) >> 2, ntiles = NT * (NT + 1) / 2;
+  T a[SW][16];
+  int tI[SW], tJ[SW];
+#pragma unroll
+  for (int s = 0; s < SW; ++s) {
+    const int t = tid + s * NTHREADS;
+    int I = -1, J = 0;
+    if (t < ntiles) tile_of(t, I, J);
+    tI[s] = I;
+    tJ[s] = J;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        a[s][r * 4 + c] = (I >= 0) ? k3_elem(n, m1, N, Q, A, G, 4 * I + r, 4 * J + c) : T(0);
+  }
+  for (int k = 0; k < m1; ++k) {
+    T* c = cb + (k & 1) * (4 * NT);
+    const int K = k >> 2, kc = k & 3;
+#pragma unroll
+    for (int s = 0; s < SW; ++s) {
+      const int I = tI[s], J = tJ[s];
+      if (I < 0) continue;
+      if (J == K) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          c[4 * I + r] = sel4(a[s][r * 4 + 0], a[s][r * 4 + 1], a[s][r * 4 + 2], a[s][r * 4 + 3], kc);
+      } else if (I == K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          c[4 * J + q] = sel4(a[s][0 + q], a[s][4 + q], a[s][8 + q], a[s][12 + q], kc);
+      }
+    }
+    __syncthreads();
+    const T d = c[k];
+    const bool good = (k < n) ? (d > T(0)) : (d < T(0));
+    if (!good || !isfinite(d)) return false;
+    const T dinv = T(1) / d;
+#pragma unroll
+    for (int s = 0; s < SW; ++s) {
+      const int I = tI[s], J = tJ[s];
+      if (I < 0) continue;
+      T ci[4], cj[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) { ci[r] = c[4 * I + r]; cj[r] = c[4 * J + r] * dinv; }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[s][r * 4 + q] = fma(-ci[r], cj[q], a[s][r * 4 + q]);
+      if (I == K || J == K) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = 4 * I + r, j = 4 * J + q;
+            if (i == k && j == k) a[s][r * 4 + q] = -dinv;
+            else if (i == k) a[s][r * 4 + q] = cj[q];
+            else if (j == k) a[s][r * 4 + q] = ci[r] * dinv;
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < SW; ++s) {
+    const int I = tI[s], J = tJ[s];
+    if (I < 0) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * I + r, j = 4 * J + q;
+        if (i >= N || j > i) continue;
+        const T v = a[s][r * 4 + q];
+        if (i < m1) {
+          SR[(size_t)i * ldS + j] = -v;
+          SR[(size_t)j * ldS + i] = -v;
+        } else if (j < m1) {
+          SR[(size_t)i * ldS + j] = v;
+        } else if (i == j) {
+          dM[i - m1] = -v;
+        } else {
+          Mb[(size_t)(j - m1) * ldM + (i - m1)] = -v;
+        }
+      }
+  }
+  return true;
+}
+
+// Cholesky factorisation M + D(dsh) = L Lᵀ with X = L⁻¹ accumulated in the same loop
+// (right-looking, one barrier per column).  M comes from the strict upper triangle of Mb
+// plus dM; X is written to the lower triangle (with diagonal) of Mb.  Step k:
+//   c = column k of the trailing matrix, d = c_k, l = c/√d;
+//   trailing update a_ij −= c_i c_j / d (i ≥ j > k);
+//   X ← L_k⁻¹ X: row k of X scaled by 1/√d, rows i > k: X_i −= c_i X_k / d.
+// A non-positive or non-finite pivot makes every thread return false.
+template <typename T, int CH>
+__device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const T* dsh, T* cb) {
+  const int tid = threadIdx.x;
+  const int NT = (p + 3) >> 2, ntiles = NT * (NT + 1) / 2;
+  T a[CH][16], x[CH][16];
+  int tI[CH], tJ[CH];
+#pragma unroll
+  for (int s = 0; s < CH; ++s) {
+    const int t = tid + s * NTHREADS;
+    int I = -1, J = 0;
+    if (t < ntiles) tile_of(t, I, J);
+    tI[s] = I;
+    tJ[s] = J;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * I + r, j = 4 * J + q;
+        T av = T(0), xv = T(0);
+        if (I >= 0) {
+          if (i >= p || j >= p) {
+            av = (i == j) ? T(1) : T(0);
+          } else if (i == j) {
+            av = dM[i] + dsh[i];
+          } else {
+            av = Mb[(size_t)min(i, j) * ldM + max(i, j)];
+          }
+          xv = (i == j) ? T(1) : T(0);
+        }
+        a[s][r * 4 + q] = av;
+        x[s][r * 4 + q] = xv;
+      }
+  }
+  for (int k = 0; k < p; ++k) {
+    T* c = cb + (k & 1) * (8 * NT);
+    T* xr = c + 4 * NT;
+    const int K = k >> 2, kc = k & 3;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int I = tI[s], J = tJ[s];
+      if (I < 0) continue;
+      if (J == K) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const T v = sel4(a[s][r * 4 + 0], a[s][r * 4 + 1], a[s][r * 4 + 2], a[s][r * 4 + 3], kc);
+          c[4 * I + r] = (4 * I + r >= k) ? v : T(0);
+        }
+      }
+      if (I == K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          xr[4 * J + q] = sel4(x[s][0 + q], x[s][4 + q], x[s][8 + q], x[s][12 + q], kc);
+      }
+    }
+    __syncthreads();
+    const T d = c[k];
+    if (!(d > T(0)) || !isfinite(d)) return false;
+    const T sq = sqrt(d);
+    const T inv = T(1) / sq;
+    const T dinv = inv * inv;
+#pragma unroll
+    for (int s = 0; s < CH; ++s) {
+      const int I = tI[s], J = tJ[s];
+      if (I < 0 || 4 * I + 3 < k) continue;
+      T ci[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) ci[r] = c[4 * I + r] * dinv;
+      if (J >= K) {
+        T cj[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cj[q] = c[4 * J + q];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a[s][r * 4 + q] = fma(-ci[r], cj[q], a[s][r * 4 + q]);
+      }
+      if (J <= K) {
+        T xj[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xj[q] = xr[4 * J + q];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) x[s][r * 4 + q] = fma(-ci[r], xj[q], x[s][r * 4 + q]);
+        if (I == K) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r == kc) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) x[s][r * 4 + q] = xj[q] * inv;
+            }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < CH; ++s) {
+    const int I = tI[s], J = tJ[s];
+    if (I < 0) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * I + r, j = 4 * J + q;
+        if (i < p && j <= i) Mb[(size_t)i * ldM + j] = x[s][r * 4 + q];
+      }
+  }
+  __syncthreads();
+  return true;
+}
+
+// out = Xᵀ(X·rhs) = (M + D)⁻¹ rhs with X = L⁻¹ in the lower triangle of Mb.
+template <typename T>
+__device__ __forceinline__ void chol_solve(int p, const T* Mb, int ldM, const T* rhs, T* y,
+                                           T* out, T* scr) {
+  mv_rows<8>(Mb, ldM, p, p, true, rhs, [&](int r, T v) { y[r] = v; });
+  __syncthreads();
+  mv_cols(Mb, ldM, p, p, true, y, scr, [&](int c, T v) { out[c] = v; });
+}
+
+// ------------------------------------------------------------------ forward kernel
+template <typename T, int SW, int CH>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> P) {
+  using V = typename Split<T>::V;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int bi = blockIdx.x, tid = threadIdx.x;
+  const int n = P.n, p = P.p, m = P.m;
+  FwdSmem<T> L;
+  L.init(n, p, m);
+  const int m1 = L.m1;
+  T* SR = reinterpret_cast<T*>(sm + L.oSR);
+  T* Mb = reinterpret_cast<T*>(sm + L.oMb);
+  T* dM = reinterpret_cast<T*>(sm + L.odM);
+  T* cb = reinterpret_cast<T*>(sm + L.ocb);
+  double* dv = reinterpret_cast<double*>(sm + L.odbl);
+  double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
+  double *rz = nu + m, *rl = rz + n, *rn = rl + p, *dsv = rn + m, *dsa = dsv + p;
+  V* xs = reinterpret_cast<V*>(sm + L.osplit);
+  T* tv = reinterpret_cast<T*>(sm + L.ovec);
+  T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *dla = dl + p;
+  T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p;
+  double* red = reinterpret_cast<double*>(sm + L.ored);
+  double* scr = reinterpret_cast<double*>(sm + L.oscr);
+  T* tscr = reinterpret_cast<T*>(scr);
+
+  const T* Qb = P.Q + (size_t)bi * n * n;
+  const T* qb = P.q + (size_t)bi * n;
+  const T* Gb = p ? P.G + (size_t)bi * p * n : nullptr;
+  const T* hb = p ? P.h + (size_t)bi * p : nullptr;
+  const T* Ab = m ? P.A + (size_t)bi * m * n : nullptr;
+  const T* bb = m ? P.b + (size_t)bi * m : nullptr;
+  WsLayout W;
+  W.init(n, p, m, (int)sizeof(T));
+  unsigned char* wsb = P.ws + (size_t)bi * P.ws_inst;
+  T* wSR = reinterpret_cast<T*>(wsb + W.oSR);
+  T* wX = reinterpret_cast<T*>(wsb + W.oX);
+  double* wIt = reinterpret_cast<double*>(wsb + W.oIt);
+  int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
+
+  int status = ST_CONV, it = 0;
+  bool ok = sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
+  __syncthreads();
+  if (!ok) status = ST_NOTPD;
+
+  double sq = 1.0, sh = 1.0, sb = 1.0;   // 1 + ‖q‖∞, 1 + ‖h‖∞, 1 + ‖b‖∞
+  if (ok) {
+    for (int i = tid; i < (m1 + p) * m1; i += NTHREADS) wSR[i] = SR[i];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < n; i += NTHREADS) v[0] = fmax(v[0], fabs((double)qb[i]));
+    for (int i = tid; i < p; i += NTHREADS) v[1] = fmax(v[1], fabs((double)hb[i]));
+    for (int i = tid; i < m; i += NTHREADS) v[2] = fmax(v[2], fabs((double)bb[i]));
+    block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+    sq = 1.0 + v[0];
+    sh = 1.0 + v[1];
+    sb = 1.0 + v[2];
+  }
+
+  if (ok && p == 0) {
+    // Equality-constrained QP: [z; ν] = S·[−q; b], then FP64-residual refinement.
+    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : bb[i - n];
+    __syncthreads();
+    mv_rows<8>(SR, L.ldS, m1, m1, false, u, [&](int r, T val) {
+      if (r < n) z[r] = (double)val; else nu[r - n] = (double)val;
+    });
+    __syncthreads();
+    for (int rs = 0; rs < 6; ++rs) {
+      for (int i = tid; i < n + m; i += NTHREADS) xs[i] = Split<T>::make(i < n ? z[i] : nu[i - n]);
+      __syncthreads();
+      kkt_apply<T>(n, 0, m, Qb, Gb, Ab, xs, scr,
+                   [&](int j) { return (double)qb[j]; }, [&](int) { return 0.0; },
+                   [&](int i) { return -(double)bb[i]; }, rz, rl, rn);
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = tid; i < n; i += NTHREADS) v[0] = rop<R_MAX>(v[0], fabs(rz[i]));
+      for (int i = tid; i < m; i += NTHREADS) v[1] = rop<R_MAX>(v[1], fabs(rn[i]));
+      block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+      if (!(v[0] == v[0]) || !(v[1] == v[1]) || isinf(v[0]) || isinf(v[1])) { status = ST_NUM; break; }
+      if (v[0] <= 0.01 * P.tol * sq && v[1] <= 0.01 * P.tol * sb) break;
+      for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
+      __syncthreads();
+      mv_rows<8>(SR, L.ldS, m1, m1, false, u, [&](int r, T val) {
+        if (r < n) z[r] += (double)val; else nu[r - n] += (double)val;
+      });
+      __syncthreads();
+    }
+  } else if (ok) {
+    // ---- initial point: the KKT solve with D(s/λ) = I, then shift s and λ positive.
+    for (int i = tid; i < p; i += NTHREADS) dsh[i] = T(1);
+    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : bb[i - n];
+    __syncthreads();
+    ok = chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb);
+    if (!ok) status = ST_NOTPD;
+    if (ok) {
+      mv_rows<8>(SR, L.ldS, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+      __syncthreads();
+      for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] - hb[i];
+      __syncthreads();
+      chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
+      mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, false, dl, tscr,
+              [&](int c, T val) { dzn[c] = wv[c] - val; });
+      double v[4] = {-INFINITY, 0.0, -INFINITY, 0.0};
+      for (int i = tid; i < n; i += NTHREADS) z[i] = (double)dzn[i];
+      for (int i = tid; i < m; i += NTHREADS) nu[i] = (double)dzn[n + i];
+      for (int i = tid; i < p; i += NTHREADS) {
+        const double lh = (double)dl[i];
+        v[0] = fmax(v[0], lh);          // max(−s) with s = −λ̂
+        v[1] += lh * lh;
+        v[2] = fmax(v[2], -lh);         // max(−λ) with λ = λ̂
+      }
+      block_reduce4<R_MAX, R_SUM, R_MAX, R_SUM>(v, red);
+      const double nrm = sqrt(v[1]);
+      const double shs = (v[0] >= -1e-8 * fmax(nrm, 1.0)) ? 1.0 + v[0] : 0.0;
+      const double shl = (v[2] >= -1e-8 * fmax(nrm, 1.0)) ? 1.0 + v[2] : 0.0;
+      for (int i = tid; i < p; i += NTHREADS) {
+        const double lh = (double)dl[i];
+        s[i] = -lh + shs;
+        lam[i] = lh + shl;
+      }
+      __syncthreads();
+
+      // ---- interior point iterations
+      for (it = 0;; ++it) {
+        for (int i = tid; i < n + p + m; i += NTHREADS)
+          xs[i] = Split<T>::make(i < n ? z[i] : (i < n + p ? lam[i - n] : nu[i - n - p]));
+        __syncthreads();
+        kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, scr,
+                     [&](int j) { return (double)qb[j]; },
+                     [&](int i) { return s[i] - (double)hb[i]; },
+                     [&](int i) { return -(double)bb[i]; }, rz, rl, rn);
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = tid; i < n; i += NTHREADS) v[0] = rop<R_MAX>(v[0], fabs(rz[i]));
+        for (int i = tid; i < p; i += NTHREADS) {
+          v[1] = rop<R_MAX>(v[1], fabs(rl[i]));
+          v[3] += s[i] * lam[i];
+        }
+        for (int i = tid; i < m; i += NTHREADS) v[2] = rop<R_MAX>(v[2], fabs(rn[i]));
+        block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+        const double mu = v[3] / p;
+        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(mu)) {
+          status = ST_NUM;
+          break;
+        }
+        if (v[0] <= P.tol * sq && v[1] <= P.tol * sh && v[2] <= P.tol * sb && mu <= P.mu_tol) {
+          status = ST_CONV;
+          break;
+        }
+        if (it >= P.max_iter) {
+          status = ST_MAXIT;
+          break;
+        }
+        for (int i = tid; i < p; i += NTHREADS) dsh[i] = (T)(s[i] / lam[i]);
+        for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
+        __syncthreads();
+        if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) {
+          status = ST_NOTPD;
+          break;
+        }
+        // Affine-scaling (predictor) direction, Eq. 9.
+        mv_rows<8>(SR, L.ldS, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+        __syncthreads();
+        for (int i = tid; i < p; i += NTHREADS) rhsa[i] = wv[m1 + i] + (T)(rl[i] - s[i]);
+        __syncthreads();
+        chol_solve(p, Mb, L.ldM, rhsa, y, dla, tscr);
+        double w4[4] = {INFINITY, 0.0, 0.0, 0.0};
+        for (int i = tid; i < p; i += NTHREADS) {
+          const double dlai = (double)dla[i];
+          const double dsai = -s[i] - (s[i] / lam[i]) * dlai;
+          dsa[i] = dsai;
+          if (dsai < 0.0) w4[0] = fmin(w4[0], -s[i] / dsai);
+          if (dlai < 0.0) w4[0] = fmin(w4[0], -lam[i] / dlai);
+        }
+        block_reduce4<R_MIN, R_SUM, R_SUM, R_SUM>(w4, red);
+        const double a_aff = fmin(1.0, w4[0]);
+        double w5[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = tid; i < p; i += NTHREADS)
+          w5[0] += (s[i] + a_aff * dsa[i]) * (lam[i] + a_aff * (double)dla[i]);
+        block_reduce4<R_SUM, R_SUM, R_SUM, R_SUM>(w5, red);
+        const double mu_aff = w5[0] / p;
+        const double sr = mu_aff / mu;
+        const double sigma = sr * sr * sr;
+        // Centering-plus-corrector (Eq. 10) folded into one combined solve.
+        for (int i = tid; i < p; i += NTHREADS) {
+          const double cc = sigma * mu - dsa[i] * (double)dla[i];
+          dsv[i] = cc;
+          rhs[i] = rhsa[i] + (T)(cc / lam[i]);
+        }
+        __syncthreads();
+        chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
+        mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, false, dl, tscr,
+                [&](int c, T val) { dzn[c] = wv[c] - val; });
+        double w6[4] = {INFINITY, 0.0, 0.0, 0.0};
+        for (int i = tid; i < p; i += NTHREADS) {
+          const double dli = (double)dl[i];
+          const double dsi = -s[i] + dsv[i] / lam[i] - (s[i] / lam[i]) * dli;
+          dsv[i] = dsi;
+          if (dsi < 0.0) w6[0] = fmin(w6[0], -s[i] / dsi);
+          if (dli < 0.0) w6[0] = fmin(w6[0], -lam[i] / dli);
+        }
+        block_reduce4<R_MIN, R_SUM, R_SUM, R_SUM>(w6, red);
+        const double alpha = fmin(1.0, 0.99 * w6[0]);
+        for (int i = tid; i < n; i += NTHREADS) z[i] += alpha * (double)dzn[i];
+        for (int i = tid; i < m; i += NTHREADS) nu[i] += alpha * (double)dzn[n + i];
+        for (int i = tid; i < p; i += NTHREADS) {
+          s[i] += alpha * dsv[i];
+          lam[i] += alpha * (double)dl[i];
+        }
+        __syncthreads();
+      }
+      // Factorisation at the returned iterate: the one the backward pass reuses.
+      if (status == ST_CONV || status == ST_MAXIT) {
+        for (int i = tid; i < p; i += NTHREADS) dsh[i] = (T)(s[i] / lam[i]);
+        __syncthreads();
+        if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) status = ST_NOTPD;
+      }
+    }
+  }
+
+  // ---- outputs and the state kept for the backward pass
+  const bool bad = (status == ST_NOTPD || status == ST_NUM);
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  for (int i = tid; i < n; i += NTHREADS) {
+    const double v = bad ? qnan : z[i];
+    P.z[(size_t)bi * n + i] = (T)v;
+    wIt[i] = v;
+  }
+  for (int i = tid; i < p; i += NTHREADS) {
+    const double vs = bad ? qnan : s[i], vl = bad ? qnan : lam[i];
+    if (P.lam) P.lam[(size_t)bi * p + i] = (T)vl;
+    wIt[n + i] = vs;
+    wIt[n + p + i] = vl;
+  }
+  for (int i = tid; i < m; i += NTHREADS) {
+    const double v = bad ? qnan : nu[i];
+    if (P.nu) P.nu[(size_t)bi * m + i] = (T)v;
+    wIt[n + 2 * p + i] = v;
+  }
+  if (!bad)
+    for (int i = tid; i < p * p; i += NTHREADS) wX[i] = Mb[i];
+  if (tid == 0) {
+    wSt[0] = status;
+    if (P.status) P.status[bi] = status;
+    if (P.iters) P.iters[bi] = it;
+  }
+}
+
+// ------------------------------------------------------------------ backward kernel
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> P) {
+  using V = typename Split<T>::V;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int bi = blockIdx.x, tid = threadIdx.x;
+  const int n = P.n, p = P.p, m = P.m, m1 = n + m;
+  BwdSmem<T> L;
+  L.init(n, p, m);
+  double* dv = reinterpret_cast<double*>(sm + L.odbl);
+  double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
+  double *dz = nu + m, *dlt = dz + n, *dnu = dlt + p;
+  double *rz = dnu + m, *rl = rz + n, *rn = rl + p;
+  V* xs = reinterpret_cast<V*>(sm + L.osplit);
+  T* tv = reinterpret_cast<T*>(sm + L.ovec);
+  T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *rhs = dl + p;
+  double* scr = reinterpret_cast<double*>(sm + L.oscr);
+  T* tscr = reinterpret_cast<T*>(scr);
+
+  WsLayout W;
+  W.init(n, p, m, (int)sizeof(T));
+  const unsigned char* wsb = P.ws + (size_t)bi * P.ws_inst;
+  const T* SR = reinterpret_cast<const T*>(wsb + W.oSR);
+  const T* X = reinterpret_cast<const T*>(wsb + W.oX);
+  const double* wIt = reinterpret_cast<const double*>(wsb + W.oIt);
+  const int status = reinterpret_cast<const int32_t*>(wsb + W.oSt)[0];
+  const T* Qb = P.Q + (size_t)bi * n * n;
+  const T* Gb = p ? P.G + (size_t)bi * p * n : nullptr;
+  const T* Ab = m ? P.A + (size_t)bi * m * n : nullptr;
+  const T* gz = P.dl_dz + (size_t)bi * n;
+
+  if (status == ST_NOTPD || status == ST_NUM) {
+    const T qn = (T)__longlong_as_double(0x7ff8000000000000LL);
+    if (P.dQ) for (int i = tid; i < n * n; i += NTHREADS) P.dQ[(size_t)bi * n * n + i] = qn;
+    if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[(size_t)bi * n + i] = qn;
+    if (P.dG) for (int i = tid; i < p * n; i += NTHREADS) P.dG[(size_t)bi * p * n + i] = qn;
+    if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[(size_t)bi * p + i] = qn;
+    if (P.dA) for (int i = tid; i < m * n; i += NTHREADS) P.dA[(size_t)bi * m * n + i] = qn;
+    if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[(size_t)bi * m + i] = qn;
+    return;
+  }
+  for (int i = tid; i < n + 2 * p + m; i += NTHREADS) dv[i] = wIt[i];
+  for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -gz[i] : T(0);
+  __syncthreads();
+
+  // K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z; 0; 0; 0]  (Eq. 11), reduced form.
+  mv_rows<8>(SR, m1, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+  __syncthreads();
+  if (p > 0) chol_solve(p, X, p, wv + m1, y, dl, tscr);
+  mv_cols(SR + (size_t)m1 * m1, m1, p, m1, false, dl, tscr,
+          [&](int c, T val) { dzn[c] = wv[c] - val; });
+  if (p == 0)
+    for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
+  __syncthreads();
+  for (int i = tid; i < n; i += NTHREADS) dz[i] = (double)dzn[i];
+  for (int i = tid; i < m; i += NTHREADS) dnu[i] = (double)dzn[n + i];
+  for (int i = tid; i < p; i += NTHREADS) dlt[i] = (double)dl[i];
+  __syncthreads();
+
+  // Iterative refinement with the FP64-accurate residual of the reduced system
+  //   ρ_z = Q d_z + Gᵀ d̃_λ + Aᵀ d_ν + ∂ℓ/∂z,  ρ_λ = G d_z − D(s/λ) d̃_λ,  ρ_ν = A d_z.
+  for (int rs = 0; rs < P.refine; ++rs) {
+    for (int i = tid; i < n + p + m; i += NTHREADS)
+      xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
+    __syncthreads();
+    kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, scr, [&](int j) { return (double)gz[j]; },
+                 [&](int i) { return -(s[i] / lam[i]) * dlt[i]; }, [&](int) { return 0.0; },
+                 rz, rl, rn);
+    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
+    __syncthreads();
+    mv_rows<8>(SR, m1, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+    __syncthreads();
+    for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] + (T)rl[i];
+    __syncthreads();
+    if (p > 0) chol_solve(p, X, p, rhs, y, dl, tscr);
+    mv_cols(SR + (size_t)m1 * m1, m1, p, m1, false, dl, tscr,
+            [&](int c, T val) { dzn[c] = wv[c] - val; });
+    if (p == 0)
+      for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
+    __syncthreads();
+    for (int i = tid; i < n; i += NTHREADS) dz[i] += (double)dzn[i];
+    for (int i = tid; i < m; i += NTHREADS) dnu[i] += (double)dzn[n + i];
+    for (int i = tid; i < p; i += NTHREADS) dlt[i] += (double)dl[i];
+    __syncthreads();
+  }
+
+  // Gradients of Eq. 8 with d̃_λ = D(λ*) d_λ.
+  if (P.dQ) {
+    T* o = P.dQ + (size_t)bi * n * n;
+    for (int e = tid; e < n * n; e += NTHREADS) {
+      const int i = e / n, j = e - i * n;
+      o[e] = (T)(0.5 * (dz[i] * z[j] + z[i] * dz[j]));
+    }
+  }
+  if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[(size_t)bi * n + i] = (T)dz[i];
+  if (P.dG) {
+    T* o = P.dG + (size_t)bi * p * n;
+    for (int e = tid; e < p * n; e += NTHREADS) {
+      const int i = e / n, j = e - i * n;
+      o[e] = (T)(dlt[i] * z[j] + lam[i] * dz[j]);
+    }
+  }
+  if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[(size_t)bi * p + i] = (T)(-dlt[i]);
+  if (P.dA) {
+    T* o = P.dA + (size_t)bi * m * n;
+    for (int e = tid; e < m * n; e += NTHREADS) {
+      const int i = e / n, j = e - i * n;
+      o[e] = (T)(dnu[i] * z[j] + nu[i] * dz[j]);
+    }
+  }
+  if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[(size_t)bi * m + i] = (T)(-dnu[i]);
+}
+
+}  // namespace qpk

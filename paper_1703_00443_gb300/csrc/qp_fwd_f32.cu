@@ -1,0 +1,23 @@
+// FP32 forward-kernel variants (FP32 factors, FP64-accurate residuals and iterate).
+#include "qp_launch.cuh"
+
+namespace qpk {
+
+template <int SW, int CH>
+static cudaError_t go(const FwdParams<float>& P, size_t smem, cudaStream_t st) {
+  auto k = qp_fwd_kernel<float, SW, CH>;
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<P.B, NTHREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_f32(const FwdParams<float>& P, int SW, int CH, size_t smem, cudaStream_t st) {
+  if (SW == 1 && CH == 1) return go<1, 1>(P, smem, st);
+  if (SW == 2 && CH == 1) return go<2, 1>(P, smem, st);
+  if (SW == 4 && CH == 1) return go<4, 1>(P, smem, st);
+  if (SW == 4 && CH == 2) return go<4, 2>(P, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qpk

@@ -1,0 +1,26 @@
+// qp_launch.cuh -- host-side launchers shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qp_device.cuh"
+
+namespace qpk {
+
+// Tile-slot variants compiled for the forward kernel (sweep slots SW, Cholesky slots CH).
+// Each slot holds one 4×4 tile per thread, so a variant covers symmetric matrices with
+// up to SW·512 (resp. CH·512) lower-triangular tiles.
+bool fwd_variant_exists(int esz, int SW, int CH);
+
+cudaError_t launch_fwd_f32(const FwdParams<float>& P, int SW, int CH, size_t smem, cudaStream_t st);
+cudaError_t launch_fwd_f64(const FwdParams<double>& P, int SW, int CH, size_t smem, cudaStream_t st);
+cudaError_t launch_bwd_f32(const BwdParams<float>& P, size_t smem, cudaStream_t st);
+cudaError_t launch_bwd_f64(const BwdParams<double>& P, size_t smem, cudaStream_t st);
+
+template <typename K>
+inline cudaError_t prepare_smem(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace qpk

@@ -1,0 +1,161 @@
+"""Python binding of the C ABI (argument marshalling only; every step runs in the CUDA
+library).  PyTorch provides device memory and the stream.
+
+    fwd = qp_forward(Q, q, G, h, A, b)             # z*, λ*, ν*, status, iters, workspace
+    grads = qp_backward(fwd, dl_dz)                 # dQ, dq, dG, dh, dA, db
+
+Shapes (batch-major, row-major, contiguous CUDA tensors of one dtype, float32 or float64):
+Q [B,n,n], q [B,n], G [B,nineq,n], h [B,nineq], A [B,neq,n], b [B,neq].  G/h or A/b may be
+None (or have zero rows) when there are no inequality or equality constraints.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _lib
+
+QP_F32, QP_F64 = 0, 1
+STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NOT_PD, STATUS_NUMERICAL = 0, 1, 2, 3
+
+
+class QPError(RuntimeError):
+    pass
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return QP_F32
+    if t.dtype == torch.float64:
+        return QP_F64
+    raise QPError(f"unsupported dtype {t.dtype}; use float32 or float64")
+
+
+def _check(rc: int):
+    if rc != 0:
+        lib = _lib.load()
+        raise QPError(f"qp call failed ({rc}): {lib.qp_strerror(rc).decode()}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def default_options(dtype=torch.float32) -> _lib.QPOptions:
+    lib = _lib.load()
+    o = _lib.QPOptions()
+    lib.qp_default_options(QP_F32 if dtype == torch.float32 else QP_F64, ctypes.byref(o))
+    return o
+
+
+def workspace_bytes(dtype, B, n, nineq, neq) -> int:
+    lib = _lib.load()
+    return int(lib.qp_workspace_bytes(QP_F32 if dtype == torch.float32 else QP_F64, B, n, nineq, neq))
+
+
+def supported(dtype, n, nineq, neq) -> bool:
+    lib = _lib.load()
+    return lib.qp_supported(QP_F32 if dtype == torch.float32 else QP_F64, n, nineq, neq) == 0
+
+
+def _prep(Q, q, G, h, A, b):
+    if Q.dim() != 3 or Q.shape[1] != Q.shape[2]:
+        raise QPError("Q must be [B, n, n]")
+    B, n = Q.shape[0], Q.shape[1]
+    dev, dt = Q.device, Q.dtype
+    if dev.type != "cuda":
+        raise QPError("tensors must live on a CUDA device (there is no CPU path)")
+    if G is None or G.numel() == 0:
+        G = torch.empty((B, 0, n), device=dev, dtype=dt)
+        h = torch.empty((B, 0), device=dev, dtype=dt)
+    if A is None or A.numel() == 0:
+        A = torch.empty((B, 0, n), device=dev, dtype=dt)
+        b = torch.empty((B, 0), device=dev, dtype=dt)
+    out = []
+    for name, t, shape in (("Q", Q, (B, n, n)), ("q", q, (B, n)), ("G", G, (B, G.shape[1], n)),
+                           ("h", h, (B, G.shape[1])), ("A", A, (B, A.shape[1], n)),
+                           ("b", b, (B, A.shape[1]))):
+        if tuple(t.shape) != shape:
+            raise QPError(f"{name} has shape {tuple(t.shape)}, expected {shape}")
+        if t.device != dev or t.dtype != dt:
+            raise QPError(f"{name} must be on {dev} with dtype {dt}")
+        out.append(t.contiguous())
+    return out
+
+
+@dataclasses.dataclass
+class ForwardResult:
+    z: torch.Tensor
+    lam: torch.Tensor
+    nu: torch.Tensor
+    status: torch.Tensor
+    iters: torch.Tensor
+    workspace: torch.Tensor
+    Q: torch.Tensor
+    G: torch.Tensor
+    A: torch.Tensor
+    options: _lib.QPOptions
+
+
+def alloc_workspace(dtype, B, n, nineq, neq, device) -> torch.Tensor:
+    nbytes = max(workspace_bytes(dtype, B, n, nineq, neq), 256)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=None,
+               out=None) -> ForwardResult:
+    """Solve the batch (C ABI ``qp_forward``) on the current CUDA stream."""
+    Q, q, G, h, A, b = _prep(Q, q, G, h, A, b)
+    B, n, nineq, neq = Q.shape[0], Q.shape[1], G.shape[1], A.shape[1]
+    dev, dt = Q.device, Q.dtype
+    code = _dtype_code(Q)
+    lib = _lib.load()
+    opts = options if options is not None else default_options(dt)
+    if workspace is None:
+        workspace = alloc_workspace(dt, B, n, nineq, neq, dev)
+    if out is None:
+        z = torch.empty((B, n), device=dev, dtype=dt)
+        lam = torch.empty((B, nineq), device=dev, dtype=dt)
+        nu = torch.empty((B, neq), device=dev, dtype=dt)
+        status = torch.empty((B,), device=dev, dtype=torch.int32)
+        iters = torch.empty((B,), device=dev, dtype=torch.int32)
+    else:
+        z, lam, nu, status, iters = out
+    with torch.cuda.device(dev):
+        rc = lib.qp_forward(ctypes.byref(opts), code, B, n, nineq, neq,
+                            _ptr(Q), _ptr(q), _ptr(G), _ptr(h), _ptr(A), _ptr(b),
+                            _ptr(z), _ptr(lam), _ptr(nu), _ptr(status), _ptr(iters),
+                            _ptr(workspace), workspace.numel(), _stream_handle(dev))
+    _check(rc)
+    return ForwardResult(z, lam, nu, status, iters, workspace, Q, G, A, opts)
+
+
+def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, need=(True,) * 6, options=None,
+                out=None):
+    """Gradients (dQ, dq, dG, dh, dA, db) of ℓ(z*) (C ABI ``qp_backward``); entries for which
+    ``need`` is False come back as None."""
+    Q, G, A = fwd.Q, fwd.G, fwd.A
+    B, n, nineq, neq = Q.shape[0], Q.shape[1], G.shape[1], A.shape[1]
+    dev, dt = Q.device, Q.dtype
+    dl_dz = dl_dz.to(device=dev, dtype=dt).contiguous()
+    if tuple(dl_dz.shape) != (B, n):
+        raise QPError(f"dl_dz has shape {tuple(dl_dz.shape)}, expected {(B, n)}")
+    lib = _lib.load()
+    opts = options if options is not None else fwd.options
+    shapes = [(B, n, n), (B, n), (B, nineq, n), (B, nineq), (B, neq, n), (B, neq)]
+    if out is None:
+        grads = [torch.empty(s, device=dev, dtype=dt) if w else None for s, w in zip(shapes, need)]
+    else:
+        grads = list(out)
+    with torch.cuda.device(dev):
+        rc = lib.qp_backward(ctypes.byref(opts), _dtype_code(Q), B, n, nineq, neq,
+                             _ptr(Q), _ptr(G), _ptr(A), _ptr(fwd.workspace), fwd.workspace.numel(),
+                             _ptr(dl_dz), *[_ptr(g) for g in grads], _stream_handle(dev))
+    _check(rc)
+    return tuple(grads)

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every symbol include/qp_gb300.h declares.
+Only host-side entry points are called (no kernel launch needs a GPU here)."""
+import ctypes
+import os
+import re
+
+from paper_1703_00443_gb300 import _lib
+
+HEADER = os.path.join(_lib.INCLUDE, "qp_gb300.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported():
+    lib = _lib.load()
+    names = declared_functions()
+    assert {"qp_forward", "qp_backward", "qp_workspace_bytes"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(_lib.EXPORTS), "binding does not declare every header symbol"
+
+
+def test_host_side_queries():
+    lib = _lib.load()
+    o = _lib.QPOptions()
+    lib.qp_default_options(0, ctypes.byref(o))
+    assert o.max_iter == 50 and o.refine == 1 and 0 < o.tol < 1e-6
+    lib.qp_default_options(1, ctypes.byref(o))
+    assert o.max_iter == 100 and o.tol <= 1e-12
+    assert lib.qp_workspace_bytes(0, 128, 100, 100, 50) >= 128 * (250 * 150 + 100 * 100) * 4
+    assert lib.qp_workspace_bytes(0, 0, 100, 100, 50) == 0
+    assert lib.qp_workspace_bytes(7, 1, 10, 10, 0) == 0
+    assert lib.qp_supported(0, 100, 100, 50) == 0
+    assert lib.qp_supported(1, 10, 20, 0) == 0
+    assert lib.qp_supported(0, 10, 5, 11) == 1      # more equalities than variables
+    assert lib.qp_strerror(0) == b"ok"
+
+
+def test_invalid_arguments_rejected_before_launch():
+    lib = _lib.load()
+    null = None
+    # bad dtype, negative sizes, missing pointers: all return QP_EINVAL without a launch
+    assert lib.qp_forward(null, 5, 1, 4, 2, 0, *([null] * 12), 0, null) == 1
+    assert lib.qp_forward(null, 0, 1, 0, 2, 0, *([null] * 12), 0, null) == 1
+    assert lib.qp_forward(null, 0, 1, 4, 2, 0, *([null] * 12), 0, null) == 1
+    assert lib.qp_forward(null, 0, 0, 4, 2, 0, *([null] * 12), 0, null) == 0   # empty batch
+    assert lib.qp_backward(null, 0, 1, 4, 2, 0, *([null] * 4), 0, *([null] * 8)) == 1

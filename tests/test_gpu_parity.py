@@ -1,0 +1,152 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances: FP32 path z* rel err ≤ 1e-5 and every gradient rel err ≤ 1e-4 (per instance,
+‖x − x_ref‖₂/‖x_ref‖₂); FP64 path ≤ 1e-9 on z*, λ*, ν* and ≤ 1e-8 on gradients.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward, supported
+from tests.helpers import kkt_residuals_fp64, oracle_solve_and_grad, rel_err
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+GRAD_NAMES = ("dQ", "dq", "dG", "dh", "dA", "db")
+
+
+def _to_dev(batch, dtype):
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    return [torch.from_numpy(np.ascontiguousarray(x)).to(DEV, tdt) for x in
+            (batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b)]
+
+
+def _run(batch, g, dtype):
+    T = _to_dev(batch, dtype)
+    fwd = qp_forward(*T)
+    grads = qp_backward(fwd, torch.from_numpy(np.ascontiguousarray(g)).to(T[0].device, T[0].dtype))
+    torch.cuda.synchronize()
+    out = dict(z=fwd.z.cpu().double().numpy(), lam=fwd.lam.cpu().double().numpy(),
+               nu=fwd.nu.cpu().double().numpy(), status=fwd.status.cpu().numpy(),
+               iters=fwd.iters.cpu().numpy())
+    for k, v in zip(GRAD_NAMES, grads):
+        out[k] = v.cpu().double().numpy()
+    return out
+
+
+def _compare(batch, g, out, idx, ztol, gtol, ltol=None):
+    sols, grads = oracle_solve_and_grad(batch, g, idx)
+    ez = rel_err(out["z"][idx], [s["z"] for s in sols])
+    assert ez.max() <= ztol, ("z", ez.max())
+    if ltol is not None:
+        if batch.nineq:
+            el = rel_err(out["lam"][idx], [s["lam"] for s in sols])
+            assert el.max() <= ltol, ("lam", el.max())
+        if batch.neq:
+            en = rel_err(out["nu"][idx], [s["nu"] for s in sols])
+            assert en.max() <= ltol, ("nu", en.max())
+    worst = {}
+    for k in GRAD_NAMES:
+        ref = [gr[k] for gr in grads]
+        if np.asarray(ref).size == 0:
+            continue
+        e = rel_err(out[k][idx], ref)
+        worst[k] = e.max()
+        assert e.max() <= gtol, (k, e.max(), np.argmax(e))
+    return ez.max(), worst
+
+
+def test_plain_fp64_config():
+    """Plain method in FP64: 8 QPs, n = 10, 20 inequalities, no equalities."""
+    batch = inputs.random_batch(8, 10, 20, 0, workload=inputs.WL_PLAIN, dtype=np.float64)
+    g = inputs.upstream_grad(8, 10, workload=inputs.WL_PLAIN, dtype=np.float64)
+    out = _run(batch, g, np.float64)
+    assert (out["status"] == 0).all()
+    _compare(batch, g, out, range(8), 1e-9, 1e-8, ltol=1e-8)
+
+
+@pytest.mark.parametrize("n", [10, 50, 100])
+def test_sweep_fp32(n):
+    """Timing-sweep shapes (n, nineq = n, neq = n/2), FP32 with FP64 residuals."""
+    B = 8
+    batch = inputs.random_batch(B, n, n, n // 2, workload=inputs.WL_SWEEP, dtype=np.float32)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
+    out = _run(batch, g, np.float32)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
+
+
+def test_full_batch_sampled_and_certified():
+    """The benchmark launch (B = 128, n = 100, 100 inequalities, 50 equalities): every
+    instance passes an FP64 KKT certificate, sampled instances match the oracle."""
+    B, n = 128, 100
+    batch = inputs.random_batch(B, n, n, n // 2, workload=inputs.WL_SWEEP, dtype=np.float32)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
+    out = _run(batch, g, np.float32)
+    assert (out["status"] == 0).all()
+    cert = kkt_residuals_fp64(batch, out["z"], out["lam"], out["nu"])
+    # z*, λ*, ν* are rounded to FP32 on output, which bounds what the certificate can show.
+    assert cert[:, 0].max() <= 1e-4 and cert[:, 1].max() <= 1e-5
+    assert cert[:, 2].max() <= 1e-5 and cert[:, 3].max() <= 0
+    _compare(batch, g, out, [0, 17, 64, 101, 127], 1e-5, 1e-4, ltol=1e-4)
+
+
+def test_onehot_structured():
+    """Structured one-hot QP: Q = 0.1 I, z ≥ 0, 40 dense equalities, MSE-loss gradient."""
+    B, n, neq = 16, 64, 40
+    batch = inputs.onehot_batch(B, n, neq, dtype=np.float32)
+    target = inputs.onehot_target(B, n)
+    T = _to_dev(batch, np.float32)
+    fwd = qp_forward(*T)
+    torch.cuda.synchronize()
+    z = fwd.z.cpu().double().numpy()
+    g = (2.0 / n) * (z - target)
+    out = _run(batch, g, np.float32)
+    assert (out["status"] == 0).all()
+    _compare(batch, g.astype(np.float32), out, range(B), 1e-5, 1e-4)
+
+
+@pytest.mark.parametrize("n,nineq,neq", [(7, 13, 3), (1, 2, 0), (5, 0, 2), (12, 0, 0),
+                                         (33, 9, 0), (60, 170, 10), (3, 1, 1)])
+def test_ragged_and_edge_sizes(n, nineq, neq):
+    B = 5
+    assert supported(torch.float32, n, nineq, neq)
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_PLAIN, dtype=np.float32,
+                                start=1000)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PLAIN, start=1000)
+    out = _run(batch, g, np.float32)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4)
+
+
+def test_empty_batch_is_noop():
+    T = [torch.empty((0, 4, 4), device=DEV), torch.empty((0, 4), device=DEV),
+         torch.empty((0, 3, 4), device=DEV), torch.empty((0, 3), device=DEV), None, None]
+    fwd = qp_forward(*T)
+    grads = qp_backward(fwd, torch.empty((0, 4), device=DEV))
+    assert fwd.z.shape == (0, 4) and grads[0].shape == (0, 4, 4)
+
+
+def test_indefinite_q_reports_not_pd():
+    batch = inputs.random_batch(3, 6, 8, 2, workload=inputs.WL_PLAIN, dtype=np.float32)
+    batch.Q[1] = -batch.Q[1]
+    T = _to_dev(batch, np.float32)
+    fwd = qp_forward(*T)
+    grads = qp_backward(fwd, torch.ones((3, 6), device=DEV))
+    torch.cuda.synchronize()
+    st = fwd.status.cpu().numpy()
+    assert st[0] == 0 and st[1] == 2 and st[2] == 0
+    assert torch.isnan(fwd.z[1]).all() and torch.isnan(grads[0][1]).all()
+    assert torch.isfinite(fwd.z[0]).all() and torch.isfinite(grads[0][2]).all()
+
+
+def test_instance_alone_equals_in_batch_and_deterministic():
+    batch = inputs.random_batch(16, 30, 30, 15, workload=inputs.WL_SWEEP, dtype=np.float32)
+    g = inputs.upstream_grad(16, 30)
+    full = _run(batch, g, np.float32)
+    again = _run(batch, g, np.float32)
+    one = inputs.random_batch(1, 30, 30, 15, workload=inputs.WL_SWEEP, dtype=np.float32, start=9)
+    alone = _run(one, g[9:10], np.float32)
+    for k in ("z", "lam", "nu") + GRAD_NAMES:
+        assert np.array_equal(full[k], again[k]), k
+        assert np.array_equal(full[k][9:10], alone[k]), k
