@@ -76,7 +76,9 @@ int qp_supported(int dtype, int n, int nineq, int neq);
  * In:   Q [B,n,n], q [B,n], G [B,nineq,n], h [B,nineq], A [B,neq,n], b [B,neq].
  *       G/h may be NULL when nineq = 0, A/b may be NULL when neq = 0.
  * Out:  z [B,n] = z*, lam [B,nineq] = λ*, nu [B,neq] = ν* (lam/nu may be NULL when their
- *       size is 0), status [B] (QP_STATUS_*), iters [B] (Newton steps taken).
+ *       size is 0), status [B] (QP_STATUS_*), iters [B] (Newton steps taken), and
+ *       optionally resid [B,4] (FP64): ‖Qz+q+Gᵀλ+Aᵀν‖∞, ‖Gz+s−h‖∞, ‖Az−b‖∞ and
+ *       μ = sᵀλ/nineq at the returned iterate (status/iters/resid may be NULL).
  * Work: workspace of at least qp_workspace_bytes(dtype,B,n,nineq,neq) bytes, 256-byte
  *       aligned; it keeps the factorisation at the returned iterate and the FP64 iterate
  *       for qp_backward.  It must not be modified between the two calls.
@@ -86,7 +88,7 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
                const void* Q, const void* q, const void* G, const void* h,
                const void* A, const void* b,
                void* z, void* lam, void* nu, int32_t* status, int32_t* iters,
-               void* workspace, size_t workspace_bytes, void* stream);
+               double* resid, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * qp_backward -- gradients of ℓ(z*) through the KKT conditions (§3, Eq. 7 and Eq. 8),

@@ -84,7 +84,7 @@ EXPORTS = {
     "qp_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "qp_supported": (c_int, [c_int, c_int, c_int, c_int]),
     "qp_forward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
-                   + [c_void_p] * 12 + [c_size_t, c_void_p]),
+                   + [c_void_p] * 13 + [c_size_t, c_void_p]),
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                     + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 8),
     "qp_strerror": (ctypes.c_char_p, [c_int]),

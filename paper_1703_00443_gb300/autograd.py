@@ -17,7 +17,7 @@ class QPFunction(torch.autograd.Function):
         fwd = qp_forward(Q, q, G, h, A, b, options=options)
         ctx.fwd = fwd
         ctx.shapes = (G is None, A is None)
-        ctx.mark_non_differentiable(fwd.lam, fwd.nu, fwd.status)
+        ctx.mark_non_differentiable(fwd.lam, fwd.nu)
         return fwd.z, fwd.lam, fwd.nu, fwd.status
 
     @staticmethod

@@ -121,7 +121,7 @@ int qp_supported(int dtype, int n, int nineq, int neq) {
 int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
                const void* Q, const void* q, const void* G, const void* h, const void* A,
                const void* b, void* z, void* lam, void* nu, int32_t* status, int32_t* iters,
-               void* workspace, size_t workspace_bytes, void* stream) {
+               double* resid, void* workspace, size_t workspace_bytes, void* stream) {
   if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return QP_EINVAL;
   if (B == 0) return QP_OK;
   if (!Q || !q || !z || !workspace) return QP_EINVAL;
@@ -142,14 +142,14 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
     qpk::FwdParams<float> P{B, n, nineq, neq,
                             (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
                             (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
-                            status, iters, (unsigned char*)workspace,
+                            status, iters, resid, (unsigned char*)workspace,
                             ws_inst(dtype, n, nineq, neq), o.tol, o.mu_tol, o.max_iter};
     e = qpk::launch_fwd_f32(P, sw, ch, smem, st);
   } else {
     qpk::FwdParams<double> P{B, n, nineq, neq,
                              (const double*)Q, (const double*)q, (const double*)G, (const double*)h,
                              (const double*)A, (const double*)b, (double*)z, (double*)lam,
-                             (double*)nu, status, iters, (unsigned char*)workspace,
+                             (double*)nu, status, iters, resid, (unsigned char*)workspace,
                              ws_inst(dtype, n, nineq, neq), o.tol, o.mu_tol, o.max_iter};
     e = qpk::launch_fwd_f64(P, sw, ch, smem, st);
   }

@@ -79,7 +79,7 @@ struct FwdSmem {
     }
     odbl = o;  o = align_up(o + 8 * (2 * (size_t)n + 5 * (size_t)p + 2 * (size_t)m), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
-    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 8 * (size_t)p), 16);
+    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 10 * (size_t)p), 16);
     ored = o;  o = align_up(o + 8 * 4 * NWARPS, 16);
     oscr = o;  o = align_up(o + 8 * (size_t)NTHREADS, 16);
     total = o;
@@ -108,6 +108,7 @@ struct FwdParams {
   const T *Q, *q, *G, *h, *A, *b;
   T *z, *lam, *nu;
   int32_t *status, *iters;
+  double* resid;   // optional [B, 4]: final ‖r_z‖∞, ‖Gz+s−h‖∞, ‖Az−b‖∞, μ
   unsigned char* ws;
   size_t ws_inst;
   double tol, mu_tol;
@@ -201,10 +202,13 @@ __device__ __forceinline__ void block_reduce4(double (&v)[4], double* red) {
 }
 
 // ------------------------------------------------------------------ matrix-vector products
-// y_r = Σ_c M[r·ld + c]·x[c] for r < rows (c ≤ r when `lower`), GL lanes per row.
-// Calls epi(r, y_r) once per row; the caller synchronises before reading the results.
+enum : int { TRI_ALL = 0, TRI_LOWER = 1, TRI_SUPPER = 2 };
+
+// y_r = Σ_c M[r·ld + c]·x[c] for r < rows, over all c (TRI_ALL), c ≤ r (TRI_LOWER) or
+// c > r (TRI_SUPPER); GL lanes per row.  Calls epi(r, y_r) once per row; the caller
+// synchronises before reading the results.
 template <int GL, typename T, typename F>
-__device__ __forceinline__ void mv_rows(const T* M, int ld, int rows, int cols, bool lower,
+__device__ __forceinline__ void mv_rows(const T* M, int ld, int rows, int cols, int tri,
                                         const T* x, F epi) {
   const int tid = threadIdx.x;
   const int g = tid / GL, gl = tid % GL;
@@ -213,9 +217,9 @@ __device__ __forceinline__ void mv_rows(const T* M, int ld, int rows, int cols, 
     const int r = r0 + g;
     T acc0 = T(0), acc1 = T(0);
     if (r < rows) {
-      const int cend = lower ? min(cols, r + 1) : cols;
+      const int cend = tri == TRI_LOWER ? min(cols, r + 1) : cols;
       const T* row = M + (size_t)r * ld;
-      int c = gl;
+      int c = (tri == TRI_SUPPER ? r + 1 : 0) + gl;
       for (; c + GL < cend; c += 2 * GL) {
         acc0 = fma(row[c], x[c], acc0);
         acc1 = fma(row[c + GL], x[c + GL], acc1);
@@ -229,23 +233,25 @@ __device__ __forceinline__ void mv_rows(const T* M, int ld, int rows, int cols, 
   }
 }
 
-// y_c = Σ_r M[r·ld + c]·x[r] for c < cols (r ≥ c when `lower`).  Row ranges are split over
-// the threads that share a column; partial sums meet in `scr` (NTHREADS entries).
-// Ends with a barrier, so epi's writes are visible on return.
+// y_c = Σ_r M[r·ld + c]·x[r] for c < cols, over all r (TRI_ALL), r ≥ c (TRI_LOWER) or
+// r < c (TRI_SUPPER).  Row ranges are split over the threads that share a column; partial
+// sums meet in `scr` (NTHREADS entries).  Ends with a barrier, so epi's writes are visible
+// on return.
 template <typename T, typename F>
-__device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, bool lower,
+__device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, int tri,
                                         const T* x, T* scr, F epi) {
   const int tid = threadIdx.x;
   if (cols <= 0) return;
   if (cols > NTHREADS / 2) {
     for (int c = tid; c < cols; c += NTHREADS) {
       T a0 = T(0), a1 = T(0);
-      int r = lower ? c : 0;
-      for (; r + 1 < rows; r += 2) {
+      int r = tri == TRI_LOWER ? c : 0;
+      const int rend = tri == TRI_SUPPER ? min(rows, c) : rows;
+      for (; r + 1 < rend; r += 2) {
         a0 = fma(M[(size_t)r * ld + c], x[r], a0);
         a1 = fma(M[(size_t)(r + 1) * ld + c], x[r + 1], a1);
       }
-      if (r < rows) a0 = fma(M[(size_t)r * ld + c], x[r], a0);
+      if (r < rend) a0 = fma(M[(size_t)r * ld + c], x[r], a0);
       epi(c, a0 + a1);
     }
     __syncthreads();
@@ -256,8 +262,9 @@ __device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, 
   if (part < nparts) {
     const int chunk = (rows + nparts - 1) / nparts;
     int r = part * chunk;
-    const int r1 = min(rows, r + chunk);
-    if (lower && r < c) r = c;
+    int r1 = min(rows, r + chunk);
+    if (tri == TRI_LOWER && r < c) r = c;
+    if (tri == TRI_SUPPER && r1 > c) r1 = c;
     T a0 = T(0), a1 = T(0);
     for (; r + 1 < r1; r += 2) {
       a0 = fma(M[(size_t)r * ld + c], x[r], a0);
@@ -590,9 +597,27 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
 template <typename T>
 __device__ __forceinline__ void chol_solve(int p, const T* Mb, int ldM, const T* rhs, T* y,
                                            T* out, T* scr) {
-  mv_rows<8>(Mb, ldM, p, p, true, rhs, [&](int r, T v) { y[r] = v; });
+  mv_rows<8>(Mb, ldM, p, p, TRI_LOWER, rhs, [&](int r, T v) { y[r] = v; });
   __syncthreads();
-  mv_cols(Mb, ldM, p, p, true, y, scr, [&](int c, T v) { out[c] = v; });
+  mv_cols(Mb, ldM, p, p, TRI_LOWER, y, scr, [&](int c, T v) { out[c] = v; });
+}
+
+// out = M·x with M symmetric, stored as its strict upper triangle in Mb plus diag in dM.
+template <typename T>
+__device__ __forceinline__ void mv_sym_upper(int p, const T* Mb, int ldM, const T* dM,
+                                             const T* x, T* tmp, T* out, T* scr) {
+  mv_rows<8>(Mb, ldM, p, p, TRI_SUPPER, x, [&](int r, T v) { tmp[r] = fma(dM[r], x[r], v); });
+  __syncthreads();
+  mv_cols(Mb, ldM, p, p, TRI_SUPPER, x, scr, [&](int c, T v) { out[c] = tmp[c] + v; });
+}
+
+// s/λ rounded into the factor type, kept finite and non-zero.
+template <typename T> __device__ __forceinline__ T ratio_to(double r);
+template <> __device__ __forceinline__ float ratio_to<float>(double r) {
+  return (float)fmin(fmax(r, 1e-30), 1e30);
+}
+template <> __device__ __forceinline__ double ratio_to<double>(double r) {
+  return fmin(fmax(r, 1e-300), 1e300);
 }
 
 // ------------------------------------------------------------------ forward kernel
@@ -615,7 +640,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   V* xs = reinterpret_cast<V*>(sm + L.osplit);
   T* tv = reinterpret_cast<T*>(sm + L.ovec);
   T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *dla = dl + p;
-  T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p;
+  T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p, *mdl = dsh + p, *tmp = mdl + p;
   double* red = reinterpret_cast<double*>(sm + L.ored);
   double* scr = reinterpret_cast<double*>(sm + L.oscr);
   T* tscr = reinterpret_cast<T*>(scr);
@@ -635,6 +660,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
 
   int status = ST_CONV, it = 0;
+  double last[4] = {0.0, 0.0, 0.0, 0.0};   // residual norms at the returned iterate
   bool ok = sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
   __syncthreads();
   if (!ok) status = ST_NOTPD;
@@ -656,7 +682,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     // Equality-constrained QP: [z; ν] = S·[−q; b], then FP64-residual refinement.
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : bb[i - n];
     __syncthreads();
-    mv_rows<8>(SR, L.ldS, m1, m1, false, u, [&](int r, T val) {
+    mv_rows<8>(SR, L.ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
       if (r < n) z[r] = (double)val; else nu[r - n] = (double)val;
     });
     __syncthreads();
@@ -670,11 +696,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
       for (int i = tid; i < n; i += NTHREADS) v[0] = rop<R_MAX>(v[0], fabs(rz[i]));
       for (int i = tid; i < m; i += NTHREADS) v[1] = rop<R_MAX>(v[1], fabs(rn[i]));
       block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+      last[0] = v[0];
+      last[2] = v[1];
       if (!(v[0] == v[0]) || !(v[1] == v[1]) || isinf(v[0]) || isinf(v[1])) { status = ST_NUM; break; }
       if (v[0] <= 0.01 * P.tol * sq && v[1] <= 0.01 * P.tol * sb) break;
       for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
       __syncthreads();
-      mv_rows<8>(SR, L.ldS, m1, m1, false, u, [&](int r, T val) {
+      mv_rows<8>(SR, L.ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
         if (r < n) z[r] += (double)val; else nu[r - n] += (double)val;
       });
       __syncthreads();
@@ -687,12 +715,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     ok = chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb);
     if (!ok) status = ST_NOTPD;
     if (ok) {
-      mv_rows<8>(SR, L.ldS, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+      mv_rows<8>(SR, L.ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
       __syncthreads();
       for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] - hb[i];
       __syncthreads();
       chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
-      mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, false, dl, tscr,
+      mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, TRI_ALL, dl, tscr,
               [&](int c, T val) { dzn[c] = wv[c] - val; });
       double v[4] = {-INFINITY, 0.0, -INFINITY, 0.0};
       for (int i = tid; i < n; i += NTHREADS) z[i] = (double)dzn[i];
@@ -732,6 +760,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
         for (int i = tid; i < m; i += NTHREADS) v[2] = rop<R_MAX>(v[2], fabs(rn[i]));
         block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
         const double mu = v[3] / p;
+        last[0] = v[0];
+        last[1] = v[1];
+        last[2] = v[2];
+        last[3] = mu;
         if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(mu)) {
           status = ST_NUM;
           break;
@@ -744,7 +776,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
           status = ST_MAXIT;
           break;
         }
-        for (int i = tid; i < p; i += NTHREADS) dsh[i] = (T)(s[i] / lam[i]);
+        for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>(s[i] / lam[i]);
         for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
         __syncthreads();
         if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) {
@@ -752,15 +784,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
           break;
         }
         // Affine-scaling (predictor) direction, Eq. 9.
-        mv_rows<8>(SR, L.ldS, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+        mv_rows<8>(SR, L.ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
         __syncthreads();
         for (int i = tid; i < p; i += NTHREADS) rhsa[i] = wv[m1 + i] + (T)(rl[i] - s[i]);
         __syncthreads();
         chol_solve(p, Mb, L.ldM, rhsa, y, dla, tscr);
+        mv_sym_upper(p, Mb, L.ldM, dM, dla, tmp, mdl, tscr);
+        // Δs from the complementarity row where s ≤ λ and from the primal row
+        // GΔz + Δs = −r_λ (with GΔz = RE·u − MΔλ) elsewhere: the first multiplies the
+        // FP32 error of Δλ by s/λ, which is large exactly where the second is safe.
         double w4[4] = {INFINITY, 0.0, 0.0, 0.0};
         for (int i = tid; i < p; i += NTHREADS) {
           const double dlai = (double)dla[i];
-          const double dsai = -s[i] - (s[i] / lam[i]) * dlai;
+          const double dsai = (s[i] <= lam[i])
+              ? -s[i] - (s[i] / lam[i]) * dlai
+              : -rl[i] - (double)wv[m1 + i] + (double)mdl[i];
           dsa[i] = dsai;
           if (dsai < 0.0) w4[0] = fmin(w4[0], -s[i] / dsai);
           if (dlai < 0.0) w4[0] = fmin(w4[0], -lam[i] / dlai);
@@ -782,12 +820,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
         }
         __syncthreads();
         chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
-        mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, false, dl, tscr,
+        mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, TRI_ALL, dl, tscr,
                 [&](int c, T val) { dzn[c] = wv[c] - val; });
+        mv_sym_upper(p, Mb, L.ldM, dM, dl, tmp, mdl, tscr);
         double w6[4] = {INFINITY, 0.0, 0.0, 0.0};
         for (int i = tid; i < p; i += NTHREADS) {
           const double dli = (double)dl[i];
-          const double dsi = -s[i] + dsv[i] / lam[i] - (s[i] / lam[i]) * dli;
+          const double dsi = (s[i] <= lam[i])
+              ? -s[i] + dsv[i] / lam[i] - (s[i] / lam[i]) * dli
+              : -rl[i] - (double)wv[m1 + i] + (double)mdl[i];
           dsv[i] = dsi;
           if (dsi < 0.0) w6[0] = fmin(w6[0], -s[i] / dsi);
           if (dli < 0.0) w6[0] = fmin(w6[0], -lam[i] / dli);
@@ -804,7 +845,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
       }
       // Factorisation at the returned iterate: the one the backward pass reuses.
       if (status == ST_CONV || status == ST_MAXIT) {
-        for (int i = tid; i < p; i += NTHREADS) dsh[i] = (T)(s[i] / lam[i]);
+        for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>(s[i] / lam[i]);
         __syncthreads();
         if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) status = ST_NOTPD;
       }
@@ -836,6 +877,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     wSt[0] = status;
     if (P.status) P.status[bi] = status;
     if (P.iters) P.iters[bi] = it;
+    if (P.resid) {
+      P.resid[4 * (size_t)bi + 0] = last[0];
+      P.resid[4 * (size_t)bi + 1] = last[1];
+      P.resid[4 * (size_t)bi + 2] = last[2];
+      P.resid[4 * (size_t)bi + 3] = last[3];
+    }
   }
 }
 
@@ -885,10 +932,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   __syncthreads();
 
   // K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z; 0; 0; 0]  (Eq. 11), reduced form.
-  mv_rows<8>(SR, m1, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+  mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
   __syncthreads();
   if (p > 0) chol_solve(p, X, p, wv + m1, y, dl, tscr);
-  mv_cols(SR + (size_t)m1 * m1, m1, p, m1, false, dl, tscr,
+  mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
           [&](int c, T val) { dzn[c] = wv[c] - val; });
   if (p == 0)
     for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
@@ -909,12 +956,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
                  rz, rl, rn);
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
     __syncthreads();
-    mv_rows<8>(SR, m1, m1 + p, m1, false, u, [&](int r, T val) { wv[r] = val; });
+    mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
     __syncthreads();
     for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] + (T)rl[i];
     __syncthreads();
     if (p > 0) chol_solve(p, X, p, rhs, y, dl, tscr);
-    mv_cols(SR + (size_t)m1 * m1, m1, p, m1, false, dl, tscr,
+    mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
             [&](int c, T val) { dzn[c] = wv[c] - val; });
     if (p == 0)
       for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];

@@ -96,6 +96,7 @@ class ForwardResult:
     nu: torch.Tensor
     status: torch.Tensor
     iters: torch.Tensor
+    resid: torch.Tensor
     workspace: torch.Tensor
     Q: torch.Tensor
     G: torch.Tensor
@@ -125,15 +126,17 @@ def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=
         nu = torch.empty((B, neq), device=dev, dtype=dt)
         status = torch.empty((B,), device=dev, dtype=torch.int32)
         iters = torch.empty((B,), device=dev, dtype=torch.int32)
+        resid = torch.empty((B, 4), device=dev, dtype=torch.float64)
     else:
-        z, lam, nu, status, iters = out
+        z, lam, nu, status, iters = out[:5]
+        resid = out[5] if len(out) > 5 else None
     with torch.cuda.device(dev):
         rc = lib.qp_forward(ctypes.byref(opts), code, B, n, nineq, neq,
                             _ptr(Q), _ptr(q), _ptr(G), _ptr(h), _ptr(A), _ptr(b),
                             _ptr(z), _ptr(lam), _ptr(nu), _ptr(status), _ptr(iters),
-                            _ptr(workspace), workspace.numel(), _stream_handle(dev))
+                            _ptr(resid), _ptr(workspace), workspace.numel(), _stream_handle(dev))
     _check(rc)
-    return ForwardResult(z, lam, nu, status, iters, workspace, Q, G, A, opts)
+    return ForwardResult(z, lam, nu, status, iters, resid, workspace, Q, G, A, opts)
 
 
 def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, need=(True,) * 6, options=None,

@@ -4,13 +4,30 @@ import numpy as np
 import oracle
 
 
-def rel_err(x, ref):
-    """Per-instance ‖x − ref‖₂ / max(‖ref‖₂, 1e-12) (rows = instances)."""
+def rel_err(x, ref, floor=None):
+    """Per-instance ‖x − ref‖₂ / max(‖ref‖₂, floor) (rows = instances); floor defaults to
+    1e-12 and may be a per-instance array."""
     x = np.asarray(x, dtype=np.float64).reshape(len(x), -1)
     ref = np.asarray(ref, dtype=np.float64).reshape(len(ref), -1)
     if x.shape[1] == 0:
         return np.zeros(len(x))
-    return np.linalg.norm(x - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-12)
+    fl = 1e-12 if floor is None else np.maximum(np.asarray(floor, dtype=np.float64), 1e-12)
+    return np.linalg.norm(x - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), fl)
+
+
+MATRIX_GRADS = ("dQ", "dG", "dA")
+
+
+def grad_floor(name, dl_dz, z_ref):
+    """Denominator floor for a gradient's relative error.  A gradient can vanish
+    identically at the solution (e.g. ∂z*/∂q = 0 when n constraints are active), where a
+    plain relative error is undefined; the floor is 1e-3·‖∂ℓ/∂z*‖₂, times max(1, ‖z*‖₂) for
+    the outer-product gradients dQ, dG, dA."""
+    g = np.linalg.norm(np.asarray(dl_dz, dtype=np.float64).reshape(len(dl_dz), -1), axis=1)
+    if name in MATRIX_GRADS:
+        zn = np.linalg.norm(np.asarray(z_ref, dtype=np.float64).reshape(len(z_ref), -1), axis=1)
+        return 1e-3 * g * np.maximum(1.0, zn)
+    return 1e-3 * g
 
 
 def oracle_solve_and_grad(batch, dl_dz, idx=None):

@@ -44,8 +44,8 @@ def test_invalid_arguments_rejected_before_launch():
     lib = _lib.load()
     null = None
     # bad dtype, negative sizes, missing pointers: all return QP_EINVAL without a launch
-    assert lib.qp_forward(null, 5, 1, 4, 2, 0, *([null] * 12), 0, null) == 1
-    assert lib.qp_forward(null, 0, 1, 0, 2, 0, *([null] * 12), 0, null) == 1
-    assert lib.qp_forward(null, 0, 1, 4, 2, 0, *([null] * 12), 0, null) == 1
-    assert lib.qp_forward(null, 0, 0, 4, 2, 0, *([null] * 12), 0, null) == 0   # empty batch
+    assert lib.qp_forward(null, 5, 1, 4, 2, 0, *([null] * 13), 0, null) == 1
+    assert lib.qp_forward(null, 0, 1, 0, 2, 0, *([null] * 13), 0, null) == 1
+    assert lib.qp_forward(null, 0, 1, 4, 2, 0, *([null] * 13), 0, null) == 1
+    assert lib.qp_forward(null, 0, 0, 4, 2, 0, *([null] * 13), 0, null) == 0   # empty batch
     assert lib.qp_backward(null, 0, 1, 4, 2, 0, *([null] * 4), 0, *([null] * 8)) == 1

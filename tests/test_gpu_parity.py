@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward, supported
-from tests.helpers import kkt_residuals_fp64, oracle_solve_and_grad, rel_err
+from tests.helpers import grad_floor, kkt_residuals_fp64, oracle_solve_and_grad, rel_err
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -50,7 +50,8 @@ def _compare(batch, g, out, idx, ztol, gtol, ltol=None):
         ref = [gr[k] for gr in grads]
         if np.asarray(ref).size == 0:
             continue
-        e = rel_err(out[k][idx], ref)
+        fl = grad_floor(k, np.asarray(g)[list(idx)], [s["z"] for s in sols])
+        e = rel_err(out[k][idx], ref, fl)
         worst[k] = e.max()
         assert e.max() <= gtol, (k, e.max(), np.argmax(e))
     return ez.max(), worst
