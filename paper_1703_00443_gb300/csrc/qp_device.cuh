@@ -41,12 +41,17 @@ enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Number of primal variables after padding: 0-3 decoupled dummy variables (Q = 1 on the
+// diagonal, no constraint coupling) make n + neq a multiple of 4, so the pivot blocks of
+// the setup sweep are whole 4×4 tiles.  Dummies sit after the real z entries and stay 0.
+__host__ __device__ inline int padded_nz(int n, int m) { return n + ((4 - (n + m) % 4) % 4); }
+
 // ------------------------------------------------------------------ layouts
 // Per-instance workspace (global memory) kept from forward to backward.
 struct WsLayout {
   size_t oSR, oX, oIt, oSt, inst;
   __host__ __device__ void init(int n, int p, int m, int esz) {
-    const size_t m1 = (size_t)n + m;
+    const size_t m1 = (size_t)padded_nz(n, m) + m;
     oSR = 0;
     oX = align_up(oSR + (m1 + p) * m1 * esz, 256);
     oIt = align_up(oX + (size_t)p * p * esz, 256);
@@ -58,10 +63,11 @@ struct WsLayout {
 // Dynamic shared memory of the forward kernel.
 template <typename T>
 struct FwdSmem {
-  int m1, N3, ldS, ldM, NT3, NTp;
+  int nz, m1, N3, ldS, ldM, NT3, NTp;
   size_t oSR, oMb, odM, ocb, odbl, osplit, ovec, ored, oscr, total;
   __host__ __device__ void init(int n, int p, int m) {
-    m1 = n + m;
+    nz = padded_nz(n, m);
+    m1 = nz + m;
     N3 = m1 + p;
     ldS = m1;
     ldM = p > 0 ? p : 1;
@@ -72,14 +78,14 @@ struct FwdSmem {
     oSR = o;   o = align_up(o + (size_t)(m1 + p) * ldS * es, 16);
     oMb = o;   o = align_up(o + (size_t)p * ldM * es, 16);
     odM = o;   o = align_up(o + (size_t)p * es, 16);
-    ocb = o;
+    ocb = o;   // panel buffers of the blocked factorisations (see sweep_setup, chol_inv)
     {
-      size_t a = 2 * 4 * (size_t)NT3, b = 2 * 8 * (size_t)NTp;
-      o = align_up(o + (a > b ? a : b) * es, 16);
+      size_t a = 2 * (32 * (size_t)NT3 + 16), b = 2 * (32 * (size_t)NTp + 16);
+      o = align_up(o + (a > b ? a : b) * es + 64, 16);
     }
-    odbl = o;  o = align_up(o + 8 * (2 * (size_t)n + 5 * (size_t)p + 2 * (size_t)m), 16);
+    odbl = o;  o = align_up(o + 8 * (2 * (size_t)n + 3 * (size_t)p + 2 * (size_t)m), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
-    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 10 * (size_t)p), 16);
+    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 12 * (size_t)p), 16);
     ored = o;  o = align_up(o + 8 * 4 * NWARPS, 16);
     oscr = o;  o = align_up(o + 8 * (size_t)NTHREADS, 16);
     total = o;
@@ -91,7 +97,7 @@ template <typename T>
 struct BwdSmem {
   size_t odbl, osplit, ovec, ored, oscr, total;
   __host__ __device__ void init(int n, int p, int m) {
-    const size_t m1 = (size_t)n + m, es = sizeof(T);
+    const size_t m1 = (size_t)padded_nz(n, m) + m, es = sizeof(T);
     size_t o = 0;
     odbl = o;   o = align_up(o + 8 * (3 * ((size_t)n + p + m) + 2 * (size_t)p), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
@@ -143,6 +149,10 @@ template <typename T> struct Acc;
 template <> struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
+  __device__ __forceinline__ void merge(const Acc& o) { s += o.s; }
+  __device__ __forceinline__ void shfl_merge(int off) {
+    s += __shfl_xor_sync(0xffffffffu, s, off);
+  }
   __device__ __forceinline__ double value() const { return s; }
 };
 // Double-float accumulator: a·x_hi is split exactly into p + e (FMA), p is added to hi
@@ -159,6 +169,18 @@ template <> struct Acc<float> {
     hi = t;
     lo = __fadd_rn(lo, __fadd_rn(err, fmaf(a, x.y, e)));
   }
+  // (hi, lo) += (ohi, olo) with a two-sum on the high parts.
+  __device__ __forceinline__ void merge2(float ohi, float olo) {
+    const float t = __fadd_rn(hi, ohi);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(ohi, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(olo, err));
+  }
+  __device__ __forceinline__ void merge(const Acc& o) { merge2(o.hi, o.lo); }
+  __device__ __forceinline__ void shfl_merge(int off) {
+    merge2(__shfl_xor_sync(0xffffffffu, hi, off), __shfl_xor_sync(0xffffffffu, lo, off));
+  }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
@@ -170,6 +192,45 @@ __device__ __forceinline__ double rop(double a, double b) {
   if (OP == R_SUM) return a + b;
   if (OP == R_MAX) return (a > b || a != a) ? a : b;   // propagates NaN
   return (a < b || a != a) ? a : b;
+}
+
+template <int OP>
+__device__ __forceinline__ float ropf(float a, float b) {
+  if (OP == R_SUM) return a + b;
+  if (OP == R_MAX) return (a > b || a != a) ? a : b;   // propagates NaN
+  return (a < b || a != a) ? a : b;
+}
+
+// Block-wide reduction of four floats (all threads get the results).  FP32 on purpose:
+// the FP64 pipe of this part is a small fraction of the FP32 one, and the reduced
+// quantities (norms for the stopping test, μ, step lengths) need no more than FP32.
+template <int O0, int O1, int O2, int O3>
+__device__ __forceinline__ void block_reduce4f(float (&v)[4], float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v[0] = ropf<O0>(v[0], __shfl_xor_sync(0xffffffffu, v[0], off));
+    v[1] = ropf<O1>(v[1], __shfl_xor_sync(0xffffffffu, v[1], off));
+    v[2] = ropf<O2>(v[2], __shfl_xor_sync(0xffffffffu, v[2], off));
+    v[3] = ropf<O3>(v[3], __shfl_xor_sync(0xffffffffu, v[3], off));
+  }
+  if (lane == 0) {
+    red[4 * w + 0] = v[0];
+    red[4 * w + 1] = v[1];
+    red[4 * w + 2] = v[2];
+    red[4 * w + 3] = v[3];
+  }
+  __syncthreads();
+  float r0 = red[0], r1 = red[1], r2 = red[2], r3 = red[3];
+#pragma unroll
+  for (int i = 1; i < NWARPS; ++i) {
+    r0 = ropf<O0>(r0, red[4 * i + 0]);
+    r1 = ropf<O1>(r1, red[4 * i + 1]);
+    r2 = ropf<O2>(r2, red[4 * i + 2]);
+    r3 = ropf<O3>(r3, red[4 * i + 3]);
+  }
+  v[0] = r0; v[1] = r1; v[2] = r2; v[3] = r3;
+  __syncthreads();
 }
 
 template <int O0, int O1, int O2, int O3>
@@ -286,52 +347,81 @@ __device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, 
 //   out_z = Q x_z + Gᵀ x_λ + Aᵀ x_ν + add_z,  out_λ = G x_z + add_λ,  out_ν = A x_z + add_ν.
 // x = [x_z; x_λ; x_ν] is given split (FP32 hi/lo pairs for T = float).  Q is symmetric, so
 // Q x_z is formed column-wise together with Gᵀx_λ and Aᵀx_ν from one pass over the rows of
-// [Q; G; A].  Ends with a barrier.
+// [Q; G; A].  Partial sums stay double-float until one conversion per output element.
+// `scr` holds NTHREADS accumulators.  Ends with a barrier.
 template <typename T, typename FZ, typename FL, typename FN>
 __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* Q, const T* G,
                                           const T* A, const typename Split<T>::V* xv,
-                                          double* scr, FZ add_z, FL add_l, FN add_n,
+                                          Acc<T>* scr, FZ add_z, FL add_l, FN add_n,
                                           double* out_z, double* out_l, double* out_n) {
   const int tid = threadIdx.x;
   const int R = n + p + m;
   const bool split_rows = (n <= NTHREADS / 2);
   const int nparts = split_rows ? NTHREADS / n : 1;
+  // Row r of the stacked matrix [Q; G; A] (the inputs stay in global memory, L2-resident).
+  auto rowp = [&](int r) -> const T* {
+    return r < n ? Q + (size_t)r * n : (r < n + p ? G + (size_t)(r - n) * n : A + (size_t)(r - n - p) * n);
+  };
+  // Column-wise pass: thread (j, part) sums rows [r0, r1) of column j.  Loads go out in
+  // unrolled batches of 24 so that a whole batch is in flight before the first use.
+  constexpr int BT = 24;
   if (split_rows) {
     const int j = tid % n, part = tid / n;
     if (part < nparts) {
       const int chunk = (R + nparts - 1) / nparts;
       const int r0 = part * chunk, r1 = min(R, r0 + chunk);
       Acc<T> acc;
-      for (int r = r0, e = min(r1, n); r < e; ++r) acc.add(Q[(size_t)r * n + j], xv[r]);
-      for (int r = max(r0, n), e = min(r1, n + p); r < e; ++r)
-        acc.add(G[(size_t)(r - n) * n + j], xv[r]);
-      for (int r = max(r0, n + p); r < r1; ++r) acc.add(A[(size_t)(r - n - p) * n + j], xv[r]);
-      scr[part * n + j] = acc.value();
+      for (int rb = r0; rb < r1; rb += BT) {
+        T av[BT];
+#pragma unroll
+        for (int u = 0; u < BT; ++u) av[u] = (rb + u < r1) ? __ldg(rowp(rb + u) + j) : T(0);
+#pragma unroll
+        for (int u = 0; u < BT; ++u)
+          if (rb + u < r1) acc.add(av[u], xv[rb + u]);
+      }
+      scr[part * n + j] = acc;
     }
   } else {
     for (int j = tid; j < n; j += NTHREADS) {
       Acc<T> acc;
-      for (int r = 0; r < n; ++r) acc.add(Q[(size_t)r * n + j], xv[r]);
-      for (int r = 0; r < p; ++r) acc.add(G[(size_t)r * n + j], xv[n + r]);
-      for (int r = 0; r < m; ++r) acc.add(A[(size_t)r * n + j], xv[n + p + r]);
+      for (int rb = 0; rb < R; rb += BT) {
+        T av[BT];
+#pragma unroll
+        for (int u = 0; u < BT; ++u) av[u] = (rb + u < R) ? __ldg(rowp(rb + u) + j) : T(0);
+#pragma unroll
+        for (int u = 0; u < BT; ++u)
+          if (rb + u < R) acc.add(av[u], xv[rb + u]);
+      }
       out_z[j] = acc.value() + add_z(j);
     }
   }
+  // Row pass: G x_z and A x_z, GL lanes per row, each lane's columns loaded in one batch.
   {
-    constexpr int GL = 8, NG = NTHREADS / GL;
+    constexpr int GL = 8, NG = NTHREADS / GL, BC = 16;
     const int g = tid / GL, gl = tid % GL;
     for (int r0 = 0; r0 < p + m; r0 += NG) {
       const int r = r0 + g;
-      double v = 0.0;
+      Acc<T> acc;
       if (r < p + m) {
-        const T* row = (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
-        Acc<T> acc;
-        for (int c = gl; c < n; c += GL) acc.add(row[c], xv[c]);
-        v = acc.value();
+        const T* __restrict__ row = (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
+        for (int cb0 = 0; cb0 < n; cb0 += GL * BC) {
+          T av[BC];
+#pragma unroll
+          for (int u = 0; u < BC; ++u) {
+            const int c = cb0 + gl + u * GL;
+            av[u] = (c < n) ? __ldg(row + c) : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < BC; ++u) {
+            const int c = cb0 + gl + u * GL;
+            if (c < n) acc.add(av[u], xv[c]);
+          }
+        }
       }
 #pragma unroll
-      for (int off = GL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      for (int off = GL / 2; off > 0; off >>= 1) acc.shfl_merge(off);
       if (r < p + m && gl == 0) {
+        const double v = acc.value();
         if (r < p) out_l[r] = v + add_l(r);
         else out_n[r - p] = v + add_n(r - p);
       }
@@ -339,9 +429,9 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* Q, const
   }
   __syncthreads();
   if (split_rows && tid < n) {
-    double s = 0.0;
-    for (int q = 0; q < nparts; ++q) s += scr[q * n + tid];
-    out_z[tid] = s + add_z(tid);
+    Acc<T> acc = scr[tid];
+    for (int q = 1; q < nparts; ++q) acc.merge(scr[q * n + tid]);
+    out_z[tid] = acc.value() + add_z(tid);
   }
   __syncthreads();
 }
@@ -362,32 +452,95 @@ __device__ __forceinline__ T sel4(T a0, T a1, T a2, T a3, int k) {
   return k == 0 ? a0 : (k == 1 ? a1 : (k == 2 ? a2 : a3));
 }
 
-// Element (i, j) of the symmetric matrix [[Q, Aᵀ, Gᵀ], [A, 0, 0], [G, 0, 0]] whose first
-// m1 = n + neq pivots are swept (rows ordered z, ν, λ).  Zero outside N×N.
+// Element (i, j) of the symmetric matrix [[Q̃, Aᵀ, Gᵀ], [A, 0, 0], [G, 0, 0]] whose first
+// m1 = nz + neq pivots are swept (rows ordered z, dummies, ν, λ; Q̃ = Q ⊕ I on the dummy
+// variables).  Zero outside N×N.
 template <typename T>
-__device__ __forceinline__ T k3_elem(int n, int m1, int N, const T* Q, const T* A, const T* G,
-                                     int i, int j) {
+__device__ __forceinline__ T k3_elem(int n, int nz, int m1, int N, const T* Q, const T* A,
+                                     const T* G, int i, int j) {
   if (i >= N || j >= N) return T(0);
   if (i < j) { const int t = i; i = j; j = t; }
   if (i < n) return Q[(size_t)i * n + j];
+  if (i < nz) return (i == j) ? T(1) : T(0);
   if (j >= n) return T(0);
-  if (i < m1) return A[(size_t)(i - n) * n + j];
+  if (i < m1) return A[(size_t)(i - nz) * n + j];
   return G[(size_t)(i - m1) * n + j];
 }
 
-// Symmetric Gauss-Jordan sweep (pivots 0 .. m1−1) of the matrix above, held in registers.
-// SWEEP(k): d = a_kk; a_kk ← −1/d; a_ik ← a_ik/d (i ≠ k); a_ij ← a_ij − a_ik a_kj / d.
-// Afterwards the top-left block is −K11⁻¹ = −S, the bottom-left block is RE = [G 0]·S and
-// the bottom-right block is −M.  Writes S and RE to SR (rows 0..m1−1 = S, m1.. = RE,
-// leading dimension ldS), M's strict upper triangle to Mb and diag(M) to dM.
-// The pivots must be positive for k < n (Q ≻ 0) and negative for k ≥ n (A of full row
-// rank); otherwise every thread returns false.
+// 4×4 tile helpers (row-major 16-element arrays, compile-time indices only).
+template <typename T>
+__device__ __forceinline__ void ld16(T (&d)[16], const T* src) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) d[e] = src[e];
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* dst, const T (&v)[16]) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) dst[e] = v[e];
+}
+
+// Four consecutive elements (16-byte aligned for float, 32-byte for double).
+__device__ __forceinline__ void ld4(float (&v)[4], const float* p) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(double (&v)[4], const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
+// Panel buffers hold 4×4 blocks column-major by pivot: element (row r of block B, pivot
+// column q) lives at q·ld + 4B + r with ld = 4·NT, so the four rows of a block for one
+// pivot are one aligned vector and neighbouring blocks are neighbouring vectors (no shared
+// memory bank conflicts when threads handle neighbouring blocks).
+template <typename T>
+__device__ __forceinline__ void ld_panel(T (&v)[16], const T* buf, int ld, int B) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    T t[4];
+    ld4(t, buf + q * ld + 4 * B);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r * 4 + q] = t[r];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st_panel(T* buf, int ld, int B, const T (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) st4(buf + q * ld + 4 * B, v[0 * 4 + q], v[1 * 4 + q], v[2 * 4 + q], v[3 * 4 + q]);
+}
+
+// Blocked symmetric Gauss-Jordan sweep over the pivots 0 .. m1−1 (m1 a multiple of 4) of
+// the matrix above, held in registers as 4×4 tiles.  SWEEP(k) is
+//   d = a_kk;  a_ij ← a_ij − a_ik a_kj / d (i, j ≠ k);  a_ik ← a_ik / d;  a_kk ← −1/d.
+// The four pivots of tile K are applied with two barriers: one thread sweeps the pivot tile
+// itself (checking each pivot's sign: positive for z rows since Q ≻ 0, negative for ν rows
+// since A has full row rank) and publishes, for each pivot k, the row r_k = (pivot-tile
+// row k before pivot k)/d_k; the owners of block row/column K replay the four scalar
+// sweeps on each of their panel rows, which yields the pivot columns ĉ_k seen by each pivot
+// and the new panel values, and publish ĉ and ĉ·D⁻¹; every other tile then takes the
+// accumulated update A_IJ −= Σ_k ĉ_Ik ĉ_Jk / d_k.  This is the scalar sweep's arithmetic,
+// so the explicit inverse of the pivot tile is never used.  Afterwards the top-left block is
+// −K11⁻¹ = −S, the bottom-left block is RE = [G 0]·S and the bottom-right block is −M.
+// Writes S and RE to SR (rows 0..m1−1 = S, m1.. = RE, leading dimension ldS), M's strict
+// upper triangle to Mb and diag(M) to dM.  Returns false on every thread if a pivot has the
+// wrong sign or is not finite.
 template <typename T, int SW>
 __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restrict__ Q,
                                          const T* __restrict__ A, const T* __restrict__ G,
                                          T* SR, int ldS, T* Mb, int ldM, T* dM, T* cb) {
   const int tid = threadIdx.x;
-  const int m1 = n + m, N = m1 + p, NT = (N + 3) >> 2, ntiles = NT * (NT + 1) / 2;
+  const int nz = padded_nz(n, m), m1 = nz + m, N = m1 + p;
+  const int NT = (N + 3) >> 2, ntiles = NT * (NT + 1) / 2, KB = m1 >> 2;
+  // cb layout per parity: Ĉ panel [16·NT], Ĉ·D⁻¹ panel [16·NT], pivot rows R [16]; flags.
+  const int pstride = 32 * NT + 16;
+  int* flag = reinterpret_cast<int*>(cb + 2 * pstride);
   T a[SW][16];
   int tI[SW], tJ[SW];
 #pragma unroll
@@ -401,52 +554,99 @@ __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restric
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        a[s][r * 4 + c] = (I >= 0) ? k3_elem(n, m1, N, Q, A, G, 4 * I + r, 4 * J + c) : T(0);
+        a[s][r * 4 + c] =
+            (I >= 0) ? k3_elem(n, nz, m1, N, Q, A, G, 4 * I + r, 4 * J + c) : T(0);
   }
-  for (int k = 0; k < m1; ++k) {
-    T* c = cb + (k & 1) * (4 * NT);
-    const int K = k >> 2, kc = k & 3;
+  for (int K = 0; K < KB; ++K) {
+    T* Cb = cb + (K & 1) * pstride;
+    T* Pb = Cb + 16 * NT;
+    T* Rb = Pb + 16 * NT;
+    // Phase A: the four scalar sweeps on the pivot tile; publish r_k.
 #pragma unroll
     for (int s = 0; s < SW; ++s) {
-      const int I = tI[s], J = tJ[s];
-      if (I < 0) continue;
-      if (J == K) {
+      if (tI[s] == K && tJ[s] == K) {
+        T w[16];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          c[4 * I + r] = sel4(a[s][r * 4 + 0], a[s][r * 4 + 1], a[s][r * 4 + 2], a[s][r * 4 + 3], kc);
-      } else if (I == K) {
+        for (int e = 0; e < 16; ++e) w[e] = a[s][e];
+        bool good = true;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          c[4 * J + q] = sel4(a[s][0 + q], a[s][4 + q], a[s][8 + q], a[s][12 + q], kc);
+        for (int k = 0; k < 4; ++k) {
+          const T d = w[k * 4 + k];
+          const bool pos = (4 * K + k) < nz;
+          good = good && isfinite(d) && (pos ? d > T(0) : d < T(0));
+          const T dinv = T(1) / d;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) Rb[k * 4 + q] = (q == k) ? dinv : w[k * 4 + q] * dinv;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (r != k && c != k) w[r * 4 + c] = fma(-w[r * 4 + k] * dinv, w[k * 4 + c], w[r * 4 + c]);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r != k) { w[r * 4 + k] *= dinv; w[k * 4 + r] *= dinv; }
+          w[k * 4 + k] = -dinv;
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) a[s][e] = w[e];
+        flag[K & 1] = good ? 0 : 1;
       }
     }
     __syncthreads();
-    const T d = c[k];
-    const bool good = (k < n) ? (d > T(0)) : (d < T(0));
-    if (!good || !isfinite(d)) return false;
-    const T dinv = T(1) / d;
+    if (flag[K & 1]) return false;
+    // Phase B: replay the four sweeps on every panel row (rows of blocks I ≠ K).
+    {
+      T R[16];
+      ld16(R, Rb);
+#pragma unroll
+      for (int s = 0; s < SW; ++s) {
+        const int I = tI[s], J = tJ[s];
+        if (I < 0 || (I != K && J != K) || (I == K && J == K)) continue;
+        const int B = (J == K) ? I : J;   // block index of the panel rows held by this tile
+        T ch[16], cd[16];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          T v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = (J == K) ? a[s][r * 4 + q] : a[s][q * 4 + r];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const T c = v[k];
+            ch[r * 4 + k] = c;
+            cd[r * 4 + k] = c * R[k * 4 + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q != k) v[q] = fma(-c, R[k * 4 + q], v[q]);
+            v[k] = c * R[k * 4 + k];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (J == K) a[s][r * 4 + q] = v[q];
+            else a[s][q * 4 + r] = v[q];
+          }
+        }
+        st_panel(Cb, 4 * NT, B, ch);
+        st_panel(Pb, 4 * NT, B, cd);
+      }
+    }
+    __syncthreads();
+    // Phase C: A_IJ −= Σ_k (ĉ_Ik / d_k) ĉ_Jk for I, J ≠ K.
 #pragma unroll
     for (int s = 0; s < SW; ++s) {
       const int I = tI[s], J = tJ[s];
-      if (I < 0) continue;
-      T ci[4], cj[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) { ci[r] = c[4 * I + r]; cj[r] = c[4 * J + r] * dinv; }
+      if (I < 0 || I == K || J == K) continue;
+      T Pi[16], Cj[16];
+      ld_panel(Pi, Pb, 4 * NT, I);
+      ld_panel(Cj, Cb, 4 * NT, J);
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a[s][r * 4 + q] = fma(-ci[r], cj[q], a[s][r * 4 + q]);
-      if (I == K || J == K) {
+        for (int c = 0; c < 4; ++c) {
+          T acc = a[s][r * 4 + c];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int i = 4 * I + r, j = 4 * J + q;
-            if (i == k && j == k) a[s][r * 4 + q] = -dinv;
-            else if (i == k) a[s][r * 4 + q] = cj[q];
-            else if (j == k) a[s][r * 4 + q] = ci[r] * dinv;
-          }
-      }
+          for (int q = 0; q < 4; ++q) acc = fma(-Pi[r * 4 + q], Cj[c * 4 + q], acc);
+          a[s][r * 4 + c] = acc;
+        }
     }
   }
 #pragma unroll
@@ -475,17 +675,22 @@ __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restric
   return true;
 }
 
-// Cholesky factorisation M + D(dsh) = L Lᵀ with X = L⁻¹ accumulated in the same loop
-// (right-looking, one barrier per column).  M comes from the strict upper triangle of Mb
-// plus dM; X is written to the lower triangle (with diagonal) of Mb.  Step k:
-//   c = column k of the trailing matrix, d = c_k, l = c/√d;
-//   trailing update a_ij −= c_i c_j / d (i ≥ j > k);
-//   X ← L_k⁻¹ X: row k of X scaled by 1/√d, rows i > k: X_i −= c_i X_k / d.
-// A non-positive or non-finite pivot makes every thread return false.
+// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ with X = L⁻¹ formed in the same loop
+// (right-looking over 4-column blocks, two barriers per block).  M comes from the strict
+// upper triangle of Mb plus dM; X is written to the lower triangle (with diagonal) of Mb.
+// Block K:  one thread factors the diagonal tile, L_KK = chol(A_KK), and inverts it;
+//           owners form the panel L_IK = A_IK L_KK⁻ᵀ (I > K) and the new block row of X,
+//           X_KJ ← L_KK⁻¹ X_KJ (J ≤ K), and publish both;
+//           every tile updates: A_IJ −= L_IK L_JKᵀ (I ≥ J > K), X_IJ −= L_IK X_KJ (I > K ≥ J).
+// Padding rows/columns beyond p are the identity and never couple to the real ones.
+// Returns false on every thread if a pivot is not positive or not finite.
 template <typename T, int CH>
 __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const T* dsh, T* cb) {
   const int tid = threadIdx.x;
   const int NT = (p + 3) >> 2, ntiles = NT * (NT + 1) / 2;
+  // cb layout per parity: L panel [16·NT], X block row [16·NT], Linv [16]; flags after.
+  const int pstride = 32 * NT + 16;
+  int* flag = reinterpret_cast<int*>(cb + 2 * pstride);
   T a[CH][16], x[CH][16];
   int tI[CH], tJ[CH];
 #pragma unroll
@@ -515,65 +720,128 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
         x[s][r * 4 + q] = xv;
       }
   }
-  for (int k = 0; k < p; ++k) {
-    T* c = cb + (k & 1) * (8 * NT);
-    T* xr = c + 4 * NT;
-    const int K = k >> 2, kc = k & 3;
+  for (int K = 0; K < NT; ++K) {
+    T* Lb = cb + (K & 1) * pstride;
+    T* Xb = Lb + 16 * NT;
+    T* Vb = Xb + 16 * NT;
+    // Phase A: Cholesky of the diagonal tile and the inverse of its factor.
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
-      const int I = tI[s], J = tJ[s];
-      if (I < 0) continue;
-      if (J == K) {
+      if (tI[s] == K && tJ[s] == K) {
+        T l[16], li[4];
+        bool good = true;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const T v = sel4(a[s][r * 4 + 0], a[s][r * 4 + 1], a[s][r * 4 + 2], a[s][r * 4 + 3], kc);
-          c[4 * I + r] = (4 * I + r >= k) ? v : T(0);
+        for (int c = 0; c < 4; ++c) {
+          T d = a[s][c * 4 + c];
+#pragma unroll
+          for (int q = 0; q < c; ++q) d = fma(-l[c * 4 + q], l[c * 4 + q], d);
+          good = good && isfinite(d) && d > T(0);
+          const T inv = rsqrt(d);
+          li[c] = inv;
+          l[c * 4 + c] = d * inv;
+#pragma unroll
+          for (int r = c + 1; r < 4; ++r) {
+            T v = a[s][r * 4 + c];
+#pragma unroll
+            for (int q = 0; q < c; ++q) v = fma(-l[r * 4 + q], l[c * 4 + q], v);
+            l[r * 4 + c] = v * inv;
+          }
+#pragma unroll
+          for (int q = c + 1; q < 4; ++q) l[c * 4 + q] = T(0);
         }
-      }
-      if (I == K) {
+        // V = L_KK⁻¹ (lower triangular), by forward substitution on the identity.
+        T v[16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          xr[4 * J + q] = sel4(x[s][0 + q], x[s][4 + q], x[s][8 + q], x[s][12 + q], kc);
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if (r < c) { v[r * 4 + c] = T(0); continue; }
+            T acc = (r == c) ? T(1) : T(0);
+#pragma unroll
+            for (int q = c; q < r; ++q) acc = fma(-l[r * 4 + q], v[q * 4 + c], acc);
+            v[r * 4 + c] = acc * li[r];
+          }
+        st16(Vb, v);
+        flag[K & 1] = good ? 0 : 1;
       }
     }
     __syncthreads();
-    const T d = c[k];
-    if (!(d > T(0)) || !isfinite(d)) return false;
-    const T sq = sqrt(d);
-    const T inv = T(1) / sq;
-    const T dinv = inv * inv;
+    if (flag[K & 1]) return false;
+    // Phase B: panel L_IK = A_IK Vᵀ and block row X_KJ ← V X_KJ.
+    {
+      T V[16];
+      ld16(V, Vb);
+#pragma unroll
+      for (int s = 0; s < CH; ++s) {
+        const int I = tI[s], J = tJ[s];
+        if (I < 0) continue;
+        if (J == K && I > K) {
+          T Ln[16];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              T acc = T(0);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc = fma(a[s][r * 4 + q], V[c * 4 + q], acc);
+              Ln[r * 4 + c] = acc;
+            }
+          st_panel(Lb, 4 * NT, I, Ln);
+        }
+        if (I == K) {
+          T Xn[16];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              T acc = T(0);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc = fma(V[r * 4 + q], x[s][q * 4 + c], acc);
+              Xn[r * 4 + c] = acc;
+            }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) x[s][e] = Xn[e];
+          T XnT[16];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) XnT[c * 4 + r] = Xn[r * 4 + c];
+          st_panel(Xb, 4 * NT, J, XnT);
+        }
+      }
+    }
+    __syncthreads();
+    // Phase C: trailing update of A and of the rows of X below block K.
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int I = tI[s], J = tJ[s];
-      if (I < 0 || 4 * I + 3 < k) continue;
-      T ci[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) ci[r] = c[4 * I + r] * dinv;
-      if (J >= K) {
-        T cj[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cj[q] = c[4 * J + q];
+      if (I <= K) continue;
+      T Li[16];
+      ld_panel(Li, Lb, 4 * NT, I);
+      if (J > K) {
+        T Lj[16];
+        ld_panel(Lj, Lb, 4 * NT, J);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) a[s][r * 4 + q] = fma(-ci[r], cj[q], a[s][r * 4 + q]);
-      }
-      if (J <= K) {
-        T xj[4];
+          for (int c = 0; c < 4; ++c) {
+            T acc = a[s][r * 4 + c];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xj[q] = xr[4 * J + q];
+            for (int q = 0; q < 4; ++q) acc = fma(-Li[r * 4 + q], Lj[c * 4 + q], acc);
+            a[s][r * 4 + c] = acc;
+          }
+      } else {
+        T XkT[16];   // XkT[c][q] = X_KJ[q][c]
+        ld_panel(XkT, Xb, 4 * NT, J);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) x[s][r * 4 + q] = fma(-ci[r], xj[q], x[s][r * 4 + q]);
-        if (I == K) {
+          for (int c = 0; c < 4; ++c) {
+            T acc = x[s][r * 4 + c];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
-            if (r == kc) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) x[s][r * 4 + q] = xj[q] * inv;
-            }
-        }
+            for (int q = 0; q < 4; ++q) acc = fma(-Li[r * 4 + q], XkT[c * 4 + q], acc);
+            x[s][r * 4 + c] = acc;
+          }
       }
     }
   }
@@ -612,9 +880,9 @@ __device__ __forceinline__ void mv_sym_upper(int p, const T* Mb, int ldM, const 
 }
 
 // s/λ rounded into the factor type, kept finite and non-zero.
-template <typename T> __device__ __forceinline__ T ratio_to(double r);
-template <> __device__ __forceinline__ float ratio_to<float>(double r) {
-  return (float)fmin(fmax(r, 1e-30), 1e30);
+template <typename T> __device__ __forceinline__ T ratio_to(T r);
+template <> __device__ __forceinline__ float ratio_to<float>(float r) {
+  return fminf(fmaxf(r, 1e-30f), 1e30f);
 }
 template <> __device__ __forceinline__ double ratio_to<double>(double r) {
   return fmin(fmax(r, 1e-300), 1e300);
@@ -629,21 +897,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   const int n = P.n, p = P.p, m = P.m;
   FwdSmem<T> L;
   L.init(n, p, m);
-  const int m1 = L.m1;
+  const int m1 = L.m1, nz = L.nz;
   T* SR = reinterpret_cast<T*>(sm + L.oSR);
   T* Mb = reinterpret_cast<T*>(sm + L.oMb);
   T* dM = reinterpret_cast<T*>(sm + L.odM);
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
   double* dv = reinterpret_cast<double*>(sm + L.odbl);
   double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
-  double *rz = nu + m, *rl = rz + n, *rn = rl + p, *dsv = rn + m, *dsa = dsv + p;
+  double *rz = nu + m, *rl = rz + n, *rn = rl + p;
   V* xs = reinterpret_cast<V*>(sm + L.osplit);
   T* tv = reinterpret_cast<T*>(sm + L.ovec);
   T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *dla = dl + p;
   T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p, *mdl = dsh + p, *tmp = mdl + p;
-  double* red = reinterpret_cast<double*>(sm + L.ored);
-  double* scr = reinterpret_cast<double*>(sm + L.oscr);
-  T* tscr = reinterpret_cast<T*>(scr);
+  T *dsv = tmp + p, *ccv = dsv + p;
+  float* red = reinterpret_cast<float*>(sm + L.ored);
+  Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.oscr);
+  T* tscr = reinterpret_cast<T*>(sm + L.oscr);
 
   const T* Qb = P.Q + (size_t)bi * n * n;
   const T* qb = P.q + (size_t)bi * n;
@@ -660,57 +929,59 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
 
   int status = ST_CONV, it = 0;
-  double last[4] = {0.0, 0.0, 0.0, 0.0};   // residual norms at the returned iterate
+  float last[4] = {0.f, 0.f, 0.f, 0.f};   // residual norms and μ at the returned iterate
   bool ok = sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
   __syncthreads();
   if (!ok) status = ST_NOTPD;
 
-  double sq = 1.0, sh = 1.0, sb = 1.0;   // 1 + ‖q‖∞, 1 + ‖h‖∞, 1 + ‖b‖∞
+  // Stopping thresholds tol·(1 + ‖q‖∞), tol·(1 + ‖h‖∞), tol·(1 + ‖b‖∞) and mu_tol.
+  float tz = 0.f, tl = 0.f, tn = 0.f;
+  const float tol = (float)P.tol, mutol = (float)P.mu_tol;
   if (ok) {
     for (int i = tid; i < (m1 + p) * m1; i += NTHREADS) wSR[i] = SR[i];
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = tid; i < n; i += NTHREADS) v[0] = fmax(v[0], fabs((double)qb[i]));
-    for (int i = tid; i < p; i += NTHREADS) v[1] = fmax(v[1], fabs((double)hb[i]));
-    for (int i = tid; i < m; i += NTHREADS) v[2] = fmax(v[2], fabs((double)bb[i]));
-    block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
-    sq = 1.0 + v[0];
-    sh = 1.0 + v[1];
-    sb = 1.0 + v[2];
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)qb[i]));
+    for (int i = tid; i < p; i += NTHREADS) v[1] = fmaxf(v[1], fabsf((float)hb[i]));
+    for (int i = tid; i < m; i += NTHREADS) v[2] = fmaxf(v[2], fabsf((float)bb[i]));
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+    tz = tol * (1.f + v[0]);
+    tl = tol * (1.f + v[1]);
+    tn = tol * (1.f + v[2]);
   }
 
   if (ok && p == 0) {
     // Equality-constrained QP: [z; ν] = S·[−q; b], then FP64-residual refinement.
-    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : bb[i - n];
+    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : (i < nz ? T(0) : bb[i - nz]);
     __syncthreads();
     mv_rows<8>(SR, L.ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
-      if (r < n) z[r] = (double)val; else nu[r - n] = (double)val;
+      if (r < n) z[r] = (double)val; else if (r >= nz) nu[r - nz] = (double)val;
     });
     __syncthreads();
     for (int rs = 0; rs < 6; ++rs) {
       for (int i = tid; i < n + m; i += NTHREADS) xs[i] = Split<T>::make(i < n ? z[i] : nu[i - n]);
       __syncthreads();
-      kkt_apply<T>(n, 0, m, Qb, Gb, Ab, xs, scr,
+      kkt_apply<T>(n, 0, m, Qb, Gb, Ab, xs, ascr,
                    [&](int j) { return (double)qb[j]; }, [&](int) { return 0.0; },
                    [&](int i) { return -(double)bb[i]; }, rz, rl, rn);
-      double v[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int i = tid; i < n; i += NTHREADS) v[0] = rop<R_MAX>(v[0], fabs(rz[i]));
-      for (int i = tid; i < m; i += NTHREADS) v[1] = rop<R_MAX>(v[1], fabs(rn[i]));
-      block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
+      for (int i = tid; i < m; i += NTHREADS) v[1] = ropf<R_MAX>(v[1], fabsf((float)rn[i]));
+      block_reduce4f<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
       last[0] = v[0];
       last[2] = v[1];
-      if (!(v[0] == v[0]) || !(v[1] == v[1]) || isinf(v[0]) || isinf(v[1])) { status = ST_NUM; break; }
-      if (v[0] <= 0.01 * P.tol * sq && v[1] <= 0.01 * P.tol * sb) break;
-      for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
+      if (!isfinite(v[0]) || !isfinite(v[1])) { status = ST_NUM; break; }
+      if (v[0] <= 0.01f * tz && v[1] <= 0.01f * tn) break;
+      for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
       __syncthreads();
       mv_rows<8>(SR, L.ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
-        if (r < n) z[r] += (double)val; else nu[r - n] += (double)val;
+        if (r < n) z[r] += (double)val; else if (r >= nz) nu[r - nz] += (double)val;
       });
       __syncthreads();
     }
   } else if (ok) {
     // ---- initial point: the KKT solve with D(s/λ) = I, then shift s and λ positive.
     for (int i = tid; i < p; i += NTHREADS) dsh[i] = T(1);
-    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : bb[i - n];
+    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : (i < nz ? T(0) : bb[i - nz]);
     __syncthreads();
     ok = chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb);
     if (!ok) status = ST_NOTPD;
@@ -722,19 +993,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
       chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
       mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, TRI_ALL, dl, tscr,
               [&](int c, T val) { dzn[c] = wv[c] - val; });
-      double v[4] = {-INFINITY, 0.0, -INFINITY, 0.0};
+      float v[4] = {-INFINITY, 0.f, -INFINITY, 0.f};
       for (int i = tid; i < n; i += NTHREADS) z[i] = (double)dzn[i];
-      for (int i = tid; i < m; i += NTHREADS) nu[i] = (double)dzn[n + i];
+      for (int i = tid; i < m; i += NTHREADS) nu[i] = (double)dzn[nz + i];
       for (int i = tid; i < p; i += NTHREADS) {
-        const double lh = (double)dl[i];
-        v[0] = fmax(v[0], lh);          // max(−s) with s = −λ̂
+        const float lh = (float)dl[i];
+        v[0] = fmaxf(v[0], lh);          // max(−s) with s = −λ̂
         v[1] += lh * lh;
-        v[2] = fmax(v[2], -lh);         // max(−λ) with λ = λ̂
+        v[2] = fmaxf(v[2], -lh);         // max(−λ) with λ = λ̂
       }
-      block_reduce4<R_MAX, R_SUM, R_MAX, R_SUM>(v, red);
-      const double nrm = sqrt(v[1]);
-      const double shs = (v[0] >= -1e-8 * fmax(nrm, 1.0)) ? 1.0 + v[0] : 0.0;
-      const double shl = (v[2] >= -1e-8 * fmax(nrm, 1.0)) ? 1.0 + v[2] : 0.0;
+      block_reduce4f<R_MAX, R_SUM, R_MAX, R_SUM>(v, red);
+      const float nrm = sqrtf(v[1]);
+      const double shs = (v[0] >= -1e-8f * fmaxf(nrm, 1.f)) ? 1.0 + (double)v[0] : 0.0;
+      const double shl = (v[2] >= -1e-8f * fmaxf(nrm, 1.f)) ? 1.0 + (double)v[2] : 0.0;
       for (int i = tid; i < p; i += NTHREADS) {
         const double lh = (double)dl[i];
         s[i] = -lh + shs;
@@ -747,19 +1018,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
         for (int i = tid; i < n + p + m; i += NTHREADS)
           xs[i] = Split<T>::make(i < n ? z[i] : (i < n + p ? lam[i - n] : nu[i - n - p]));
         __syncthreads();
-        kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, scr,
+        kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr,
                      [&](int j) { return (double)qb[j]; },
                      [&](int i) { return s[i] - (double)hb[i]; },
                      [&](int i) { return -(double)bb[i]; }, rz, rl, rn);
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int i = tid; i < n; i += NTHREADS) v[0] = rop<R_MAX>(v[0], fabs(rz[i]));
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
         for (int i = tid; i < p; i += NTHREADS) {
-          v[1] = rop<R_MAX>(v[1], fabs(rl[i]));
-          v[3] += s[i] * lam[i];
+          v[1] = ropf<R_MAX>(v[1], fabsf((float)rl[i]));
+          v[3] += (float)s[i] * (float)lam[i];
         }
-        for (int i = tid; i < m; i += NTHREADS) v[2] = rop<R_MAX>(v[2], fabs(rn[i]));
-        block_reduce4<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
-        const double mu = v[3] / p;
+        for (int i = tid; i < m; i += NTHREADS) v[2] = ropf<R_MAX>(v[2], fabsf((float)rn[i]));
+        block_reduce4f<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+        const float mu = v[3] / (float)p;
         last[0] = v[0];
         last[1] = v[1];
         last[2] = v[2];
@@ -768,7 +1039,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
           status = ST_NUM;
           break;
         }
-        if (v[0] <= P.tol * sq && v[1] <= P.tol * sh && v[2] <= P.tol * sb && mu <= P.mu_tol) {
+        if (v[0] <= tz && v[1] <= tl && v[2] <= tn && mu <= mutol) {
           status = ST_CONV;
           break;
         }
@@ -776,8 +1047,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
           status = ST_MAXIT;
           break;
         }
-        for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>(s[i] / lam[i]);
-        for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
+        for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>((T)s[i] / (T)lam[i]);
+        for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
         __syncthreads();
         if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) {
           status = ST_NOTPD;
@@ -793,59 +1064,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
         // Δs from the complementarity row where s ≤ λ and from the primal row
         // GΔz + Δs = −r_λ (with GΔz = RE·u − MΔλ) elsewhere: the first multiplies the
         // FP32 error of Δλ by s/λ, which is large exactly where the second is safe.
-        double w4[4] = {INFINITY, 0.0, 0.0, 0.0};
+        float w4[4] = {INFINITY, 0.f, 0.f, 0.f};
         for (int i = tid; i < p; i += NTHREADS) {
-          const double dlai = (double)dla[i];
-          const double dsai = (s[i] <= lam[i])
-              ? -s[i] - (s[i] / lam[i]) * dlai
-              : -rl[i] - (double)wv[m1 + i] + (double)mdl[i];
-          dsa[i] = dsai;
-          if (dsai < 0.0) w4[0] = fmin(w4[0], -s[i] / dsai);
-          if (dlai < 0.0) w4[0] = fmin(w4[0], -lam[i] / dlai);
+          const T si = (T)s[i], li = (T)lam[i], d = dla[i];
+          const T dsai = (si <= li) ? -si - dsh[i] * d : (T)(-rl[i]) - wv[m1 + i] + mdl[i];
+          dsv[i] = dsai;
+          if (dsai < T(0)) w4[0] = fminf(w4[0], (float)(-si / dsai));
+          if (d < T(0)) w4[0] = fminf(w4[0], (float)(-li / d));
         }
-        block_reduce4<R_MIN, R_SUM, R_SUM, R_SUM>(w4, red);
-        const double a_aff = fmin(1.0, w4[0]);
-        double w5[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int i = tid; i < p; i += NTHREADS)
-          w5[0] += (s[i] + a_aff * dsa[i]) * (lam[i] + a_aff * (double)dla[i]);
-        block_reduce4<R_SUM, R_SUM, R_SUM, R_SUM>(w5, red);
-        const double mu_aff = w5[0] / p;
-        const double sr = mu_aff / mu;
-        const double sigma = sr * sr * sr;
+        block_reduce4f<R_MIN, R_SUM, R_SUM, R_SUM>(w4, red);
+        const float a_aff = fminf(1.f, w4[0]);
+        float w5[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = tid; i < p; i += NTHREADS) {
+          const T si = (T)s[i], li = (T)lam[i];
+          w5[0] += (float)((si + (T)a_aff * dsv[i]) * (li + (T)a_aff * dla[i]));
+        }
+        block_reduce4f<R_SUM, R_SUM, R_SUM, R_SUM>(w5, red);
+        const float mu_aff = w5[0] / (float)p;
+        const float sr = mu_aff / mu;
+        const T smu = (T)(sr * sr * sr * mu);
         // Centering-plus-corrector (Eq. 10) folded into one combined solve.
         for (int i = tid; i < p; i += NTHREADS) {
-          const double cc = sigma * mu - dsa[i] * (double)dla[i];
-          dsv[i] = cc;
-          rhs[i] = rhsa[i] + (T)(cc / lam[i]);
+          const T cc = smu - dsv[i] * dla[i];
+          ccv[i] = cc;
+          rhs[i] = rhsa[i] + cc / (T)lam[i];
         }
         __syncthreads();
         chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
         mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, TRI_ALL, dl, tscr,
                 [&](int c, T val) { dzn[c] = wv[c] - val; });
         mv_sym_upper(p, Mb, L.ldM, dM, dl, tmp, mdl, tscr);
-        double w6[4] = {INFINITY, 0.0, 0.0, 0.0};
+        float w6[4] = {INFINITY, 0.f, 0.f, 0.f};
         for (int i = tid; i < p; i += NTHREADS) {
-          const double dli = (double)dl[i];
-          const double dsi = (s[i] <= lam[i])
-              ? -s[i] + dsv[i] / lam[i] - (s[i] / lam[i]) * dli
-              : -rl[i] - (double)wv[m1 + i] + (double)mdl[i];
+          const T si = (T)s[i], li = (T)lam[i], d = dl[i];
+          const T dsi = (si <= li) ? -si + ccv[i] / li - dsh[i] * d
+                                   : (T)(-rl[i]) - wv[m1 + i] + mdl[i];
           dsv[i] = dsi;
-          if (dsi < 0.0) w6[0] = fmin(w6[0], -s[i] / dsi);
-          if (dli < 0.0) w6[0] = fmin(w6[0], -lam[i] / dli);
+          if (dsi < T(0)) w6[0] = fminf(w6[0], (float)(-si / dsi));
+          if (d < T(0)) w6[0] = fminf(w6[0], (float)(-li / d));
         }
-        block_reduce4<R_MIN, R_SUM, R_SUM, R_SUM>(w6, red);
-        const double alpha = fmin(1.0, 0.99 * w6[0]);
+        block_reduce4f<R_MIN, R_SUM, R_SUM, R_SUM>(w6, red);
+        const double alpha = (double)fminf(1.f, 0.99f * w6[0]);
         for (int i = tid; i < n; i += NTHREADS) z[i] += alpha * (double)dzn[i];
-        for (int i = tid; i < m; i += NTHREADS) nu[i] += alpha * (double)dzn[n + i];
+        for (int i = tid; i < m; i += NTHREADS) nu[i] += alpha * (double)dzn[nz + i];
         for (int i = tid; i < p; i += NTHREADS) {
-          s[i] += alpha * dsv[i];
+          s[i] += alpha * (double)dsv[i];
           lam[i] += alpha * (double)dl[i];
         }
         __syncthreads();
       }
       // Factorisation at the returned iterate: the one the backward pass reuses.
       if (status == ST_CONV || status == ST_MAXIT) {
-        for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>(s[i] / lam[i]);
+        for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>((T)s[i] / (T)lam[i]);
         __syncthreads();
         if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) status = ST_NOTPD;
       }
@@ -892,7 +1162,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   using V = typename Split<T>::V;
   extern __shared__ __align__(16) unsigned char sm[];
   const int bi = blockIdx.x, tid = threadIdx.x;
-  const int n = P.n, p = P.p, m = P.m, m1 = n + m;
+  const int n = P.n, p = P.p, m = P.m, nz = padded_nz(n, m), m1 = nz + m;
   BwdSmem<T> L;
   L.init(n, p, m);
   double* dv = reinterpret_cast<double*>(sm + L.odbl);
@@ -902,8 +1172,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   V* xs = reinterpret_cast<V*>(sm + L.osplit);
   T* tv = reinterpret_cast<T*>(sm + L.ovec);
   T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *rhs = dl + p;
-  double* scr = reinterpret_cast<double*>(sm + L.oscr);
-  T* tscr = reinterpret_cast<T*>(scr);
+  Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.oscr);
+  T* tscr = reinterpret_cast<T*>(sm + L.oscr);
 
   WsLayout W;
   W.init(n, p, m, (int)sizeof(T));
@@ -941,7 +1211,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
     for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
   __syncthreads();
   for (int i = tid; i < n; i += NTHREADS) dz[i] = (double)dzn[i];
-  for (int i = tid; i < m; i += NTHREADS) dnu[i] = (double)dzn[n + i];
+  for (int i = tid; i < m; i += NTHREADS) dnu[i] = (double)dzn[nz + i];
   for (int i = tid; i < p; i += NTHREADS) dlt[i] = (double)dl[i];
   __syncthreads();
 
@@ -951,10 +1221,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
     __syncthreads();
-    kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, scr, [&](int j) { return (double)gz[j]; },
+    kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, [&](int j) { return (double)gz[j]; },
                  [&](int i) { return -(s[i] / lam[i]) * dlt[i]; }, [&](int) { return 0.0; },
                  rz, rl, rn);
-    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (T)(-rn[i - n]);
+    for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
     __syncthreads();
     mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
     __syncthreads();
@@ -967,7 +1237,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
       for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
     __syncthreads();
     for (int i = tid; i < n; i += NTHREADS) dz[i] += (double)dzn[i];
-    for (int i = tid; i < m; i += NTHREADS) dnu[i] += (double)dzn[n + i];
+    for (int i = tid; i < m; i += NTHREADS) dnu[i] += (double)dzn[nz + i];
     for (int i = tid; i < p; i += NTHREADS) dlt[i] += (double)dl[i];
     __syncthreads();
   }
