@@ -64,7 +64,7 @@ struct WsLayout {
 template <typename T>
 struct FwdSmem {
   int nz, m1, N3, ldS, ldM, NT3, NTp;
-  size_t oSR, oMb, odM, ocb, odbl, osplit, ovec, ored, oscr, total;
+  size_t oSR, oMb, odM, ocb, cbytes, odbl, osplit, ovec, ored, total;
   __host__ __device__ void init(int n, int p, int m) {
     nz = padded_nz(n, m);
     m1 = nz + m;
@@ -78,16 +78,20 @@ struct FwdSmem {
     oSR = o;   o = align_up(o + (size_t)(m1 + p) * ldS * es, 16);
     oMb = o;   o = align_up(o + (size_t)p * ldM * es, 16);
     odM = o;   o = align_up(o + (size_t)p * es, 16);
-    ocb = o;   // panel buffers of the blocked factorisations (see sweep_setup, chol_inv)
+    // Work region: panel buffers of the blocked factorisations (sweep_setup, chol_inv),
+    // reused as partial-sum scratch by kkt_apply and mv_cols (never live at the same time).
+    ocb = o;
     {
       size_t a = 2 * (32 * (size_t)NT3 + 16), b = 2 * (32 * (size_t)NTp + 16);
-      o = align_up(o + (a > b ? a : b) * es + 64, 16);
+      size_t c = (a > b ? a : b) * es + 64;
+      if (c < 8 * (size_t)NTHREADS) c = 8 * (size_t)NTHREADS;
+      cbytes = align_up(c, 16);
+      o += cbytes;
     }
-    odbl = o;  o = align_up(o + 8 * (2 * (size_t)n + 3 * (size_t)p + 2 * (size_t)m), 16);
+    odbl = o;  o = align_up(o + 8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
     ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 12 * (size_t)p), 16);
     ored = o;  o = align_up(o + 8 * 4 * NWARPS, 16);
-    oscr = o;  o = align_up(o + 8 * (size_t)NTHREADS, 16);
     total = o;
   }
 };
@@ -103,7 +107,7 @@ struct BwdSmem {
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
     ovec = o;   o = align_up(o + es * (3 * m1 + 4 * (size_t)p), 16);
     ored = o;   o = align_up(o + 8 * 4 * NWARPS, 16);
-    oscr = o;   o = align_up(o + 8 * (size_t)NTHREADS, 16);
+    oscr = o;   o = align_up(o + 8 * (size_t)4 * NTHREADS, 16);
     total = o;
   }
 };
@@ -343,92 +347,186 @@ __device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, 
   __syncthreads();
 }
 
+// Four consecutive elements from global memory, read-only path (16-byte aligned).
+__device__ __forceinline__ void ldg4(float (&v)[4], const float* p) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ldg4(double (&v)[4], const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // FP64-accurate application of the (unreduced, slack-eliminated) KKT operator:
 //   out_z = Q x_z + Gᵀ x_λ + Aᵀ x_ν + add_z,  out_λ = G x_z + add_λ,  out_ν = A x_z + add_ν.
 // x = [x_z; x_λ; x_ν] is given split (FP32 hi/lo pairs for T = float).  Q is symmetric, so
 // Q x_z is formed column-wise together with Gᵀx_λ and Aᵀx_ν from one pass over the rows of
-// [Q; G; A].  Partial sums stay double-float until one conversion per output element.
-// `scr` holds NTHREADS accumulators.  Ends with a barrier.
+// [Q; G; A] (inputs read from global memory, where they stay L2-resident); G x_z and A x_z
+// come from a row pass.  When n is a multiple of 4 every thread reads four consecutive
+// columns per 16-byte load.  Partial sums stay double-float until one conversion per output
+// element.  `scr` holds kscr ≥ NTHREADS accumulators.  Ends with a barrier.
 template <typename T, typename FZ, typename FL, typename FN>
-__device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* Q, const T* G,
-                                          const T* A, const typename Split<T>::V* xv,
-                                          Acc<T>* scr, FZ add_z, FL add_l, FN add_n,
+__device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restrict__ Q,
+                                          const T* __restrict__ G, const T* __restrict__ A,
+                                          const typename Split<T>::V* xv, Acc<T>* scr, int kscr,
+                                          FZ add_z, FL add_l, FN add_n,
                                           double* out_z, double* out_l, double* out_n) {
+  using V = typename Split<T>::V;
   const int tid = threadIdx.x;
   const int R = n + p + m;
-  const bool split_rows = (n <= NTHREADS / 2);
-  const int nparts = split_rows ? NTHREADS / n : 1;
-  // Row r of the stacked matrix [Q; G; A] (the inputs stay in global memory, L2-resident).
   auto rowp = [&](int r) -> const T* {
     return r < n ? Q + (size_t)r * n : (r < n + p ? G + (size_t)(r - n) * n : A + (size_t)(r - n - p) * n);
   };
-  // Column-wise pass: thread (j, part) sums rows [r0, r1) of column j.  Loads go out in
-  // unrolled batches of 24 so that a whole batch is in flight before the first use.
-  constexpr int BT = 24;
-  if (split_rows) {
+  const bool vec4 = (n % 4 == 0) &&
+      ((((uintptr_t)Q) | ((uintptr_t)G) | ((uintptr_t)A)) % (4 * sizeof(T)) == 0);
+  int nparts = 0;   // > 0: column partials in scr[part·n + j] to be merged below
+  if (vec4) {
+    const int nq = n / 4;
+    nparts = min(NTHREADS / nq, kscr / n);
+    if (nparts >= 1) {
+      const int jq = tid % nq, part = tid / nq;
+      if (part < nparts) {
+        const int chunk = (R + nparts - 1) / nparts;
+        const int r0 = part * chunk, r1 = min(R, r0 + chunk);
+        Acc<T> acc[4];
+        int r = r0;
+        for (; r + 4 <= r1; r += 4) {
+          T av[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ldg4(av[u], rowp(r + u) + 4 * jq);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const V x = xv[r + u];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c].add(av[u][c], x);
+          }
+        }
+        for (; r < r1; ++r) {
+          T av[4];
+          ldg4(av, rowp(r) + 4 * jq);
+          const V x = xv[r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[c].add(av[c], x);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) scr[part * n + 4 * jq + c] = acc[c];
+      }
+    } else {
+      nparts = 0;
+      for (int jq = tid; jq < nq; jq += NTHREADS) {
+        Acc<T> acc[4];
+        for (int r = 0; r < R; ++r) {
+          T av[4];
+          ldg4(av, rowp(r) + 4 * jq);
+          const V x = xv[r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[c].add(av[c], x);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out_z[4 * jq + c] = acc[c].value() + add_z(4 * jq + c);
+      }
+    }
+  } else if (n <= NTHREADS / 2) {
+    nparts = min(NTHREADS, kscr) / n;
     const int j = tid % n, part = tid / n;
     if (part < nparts) {
       const int chunk = (R + nparts - 1) / nparts;
       const int r0 = part * chunk, r1 = min(R, r0 + chunk);
       Acc<T> acc;
-      for (int rb = r0; rb < r1; rb += BT) {
-        T av[BT];
+      int r = r0;
+      for (; r + 8 <= r1; r += 8) {
+        T av[8];
 #pragma unroll
-        for (int u = 0; u < BT; ++u) av[u] = (rb + u < r1) ? __ldg(rowp(rb + u) + j) : T(0);
+        for (int u = 0; u < 8; ++u) av[u] = __ldg(rowp(r + u) + j);
 #pragma unroll
-        for (int u = 0; u < BT; ++u)
-          if (rb + u < r1) acc.add(av[u], xv[rb + u]);
+        for (int u = 0; u < 8; ++u) acc.add(av[u], xv[r + u]);
       }
+      for (; r < r1; ++r) acc.add(__ldg(rowp(r) + j), xv[r]);
       scr[part * n + j] = acc;
     }
   } else {
     for (int j = tid; j < n; j += NTHREADS) {
       Acc<T> acc;
-      for (int rb = 0; rb < R; rb += BT) {
-        T av[BT];
-#pragma unroll
-        for (int u = 0; u < BT; ++u) av[u] = (rb + u < R) ? __ldg(rowp(rb + u) + j) : T(0);
-#pragma unroll
-        for (int u = 0; u < BT; ++u)
-          if (rb + u < R) acc.add(av[u], xv[rb + u]);
-      }
+      for (int r = 0; r < R; ++r) acc.add(__ldg(rowp(r) + j), xv[r]);
       out_z[j] = acc.value() + add_z(j);
     }
   }
-  // Row pass: G x_z and A x_z, GL lanes per row, each lane's columns loaded in one batch.
+  // Row pass: G x_z and A x_z with GL lanes per row, two rows per lane group at a time so
+  // that both rows' loads are in flight together.
   {
-    constexpr int GL = 8, NG = NTHREADS / GL, BC = 16;
+    constexpr int GL = 8, NG = NTHREADS / GL, QB = 4;
     const int g = tid / GL, gl = tid % GL;
-    for (int r0 = 0; r0 < p + m; r0 += NG) {
-      const int r = r0 + g;
-      Acc<T> acc;
-      if (r < p + m) {
-        const T* __restrict__ row = (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
-        for (int cb0 = 0; cb0 < n; cb0 += GL * BC) {
-          T av[BC];
+    for (int r0 = 0; r0 < p + m; r0 += 2 * NG) {
+      const int rr[2] = {r0 + g, r0 + NG + g};
+      const T* rowv[2];
 #pragma unroll
-          for (int u = 0; u < BC; ++u) {
-            const int c = cb0 + gl + u * GL;
-            av[u] = (c < n) ? __ldg(row + c) : T(0);
-          }
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int r = rr[h2];
+        rowv[h2] = (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
+      }
+      Acc<T> acc[2];
+      if (vec4) {
+        const int nq = n / 4;
+        for (int qb0 = 0; qb0 < nq; qb0 += GL * QB) {
+          T av[2][QB][4];
 #pragma unroll
-          for (int u = 0; u < BC; ++u) {
-            const int c = cb0 + gl + u * GL;
-            if (c < n) acc.add(av[u], xv[c]);
-          }
+          for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+              const int q = qb0 + gl + u * GL;
+              if (rr[h2] < p + m && q < nq) {
+                ldg4(av[h2][u], rowv[h2] + 4 * q);
+              } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) av[h2][u][c] = T(0);
+              }
+            }
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+              const int q = qb0 + gl + u * GL;
+              if (rr[h2] < p + m && q < nq) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[h2].add(av[h2][u][c], xv[4 * q + c]);
+              }
+            }
+        }
+      } else {
+        for (int cb0 = 0; cb0 < n; cb0 += GL * 8) {
+          T av[2][8];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int c = cb0 + gl + u * GL;
+              av[h2][u] = (rr[h2] < p + m && c < n) ? __ldg(rowv[h2] + c) : T(0);
+            }
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int c = cb0 + gl + u * GL;
+              if (rr[h2] < p + m && c < n) acc[h2].add(av[h2][u], xv[c]);
+            }
         }
       }
 #pragma unroll
-      for (int off = GL / 2; off > 0; off >>= 1) acc.shfl_merge(off);
-      if (r < p + m && gl == 0) {
-        const double v = acc.value();
-        if (r < p) out_l[r] = v + add_l(r);
-        else out_n[r - p] = v + add_n(r - p);
+      for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll
+        for (int off = GL / 2; off > 0; off >>= 1) acc[h2].shfl_merge(off);
+        const int r = rr[h2];
+        if (r < p + m && gl == 0) {
+          const double v = acc[h2].value();
+          if (r < p) out_l[r] = v + add_l(r);
+          else out_n[r - p] = v + add_n(r - p);
+        }
       }
     }
   }
   __syncthreads();
-  if (split_rows && tid < n) {
+  if (nparts > 0 && tid < n) {
     Acc<T> acc = scr[tid];
     for (int q = 1; q < nparts; ++q) acc.merge(scr[q * n + tid]);
     out_z[tid] = acc.value() + add_z(tid);
@@ -445,6 +543,15 @@ __device__ __forceinline__ void tile_of(int t, int& I, int& J) {
   while (i * (i + 1) / 2 > t) --i;
   I = i;
   J = t - i * (i + 1) / 2;
+}
+
+// Column-major enumeration of the lower tiles of an NT×NT tile grid: tile column J holds
+// tiles (J..NT−1, J) at consecutive indices starting at J·NT − J(J−1)/2.
+__device__ __forceinline__ void tile_of_colmajor(int t, int NT, int& I, int& J) {
+  int j = 0, off = 0;
+  while (j < NT && off + (NT - j) <= t) { off += NT - j; ++j; }
+  J = j;
+  I = j + (t - off);
 }
 
 template <typename T>
@@ -691,21 +798,28 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
   // cb layout per parity: L panel [16·NT], X block row [16·NT], Linv [16]; flags after.
   const int pstride = 32 * NT + 16;
   int* flag = reinterpret_cast<int*>(cb + 2 * pstride);
+  // A tiles are owned column-major (a tile column, i.e. a panel, sits in one or two warps);
+  // X tiles row-major (a block row of X likewise).
   T a[CH][16], x[CH][16];
-  int tI[CH], tJ[CH];
+  int tI[CH], tJ[CH], xI[CH], xJ[CH];
 #pragma unroll
   for (int s = 0; s < CH; ++s) {
     const int t = tid + s * NTHREADS;
-    int I = -1, J = 0;
-    if (t < ntiles) tile_of(t, I, J);
+    int I = -1, J = 0, XI = -1, XJ = 0;
+    if (t < ntiles) {
+      tile_of_colmajor(t, NT, I, J);
+      tile_of(t, XI, XJ);
+    }
     tI[s] = I;
     tJ[s] = J;
+    xI[s] = XI;
+    xJ[s] = XJ;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = 4 * I + r, j = 4 * J + q;
-        T av = T(0), xv = T(0);
+        T av = T(0);
         if (I >= 0) {
           if (i >= p || j >= p) {
             av = (i == j) ? T(1) : T(0);
@@ -714,10 +828,9 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
           } else {
             av = Mb[(size_t)min(i, j) * ldM + max(i, j)];
           }
-          xv = (i == j) ? T(1) : T(0);
         }
         a[s][r * 4 + q] = av;
-        x[s][r * 4 + q] = xv;
+        x[s][r * 4 + q] = (XI >= 0 && 4 * XI + r == 4 * XJ + q) ? T(1) : T(0);
       }
   }
   for (int K = 0; K < NT; ++K) {
@@ -768,46 +881,44 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
     __syncthreads();
     if (flag[K & 1]) return false;
     // Phase B: panel L_IK = A_IK Vᵀ and block row X_KJ ← V X_KJ.
-    {
-      T V[16];
-      ld16(V, Vb);
 #pragma unroll
-      for (int s = 0; s < CH; ++s) {
-        const int I = tI[s], J = tJ[s];
-        if (I < 0) continue;
-        if (J == K && I > K) {
-          T Ln[16];
+    for (int s = 0; s < CH; ++s) {
+      if (tJ[s] == K && tI[s] > K) {
+        T V[16];
+        ld16(V, Vb);
+        T Ln[16];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              T acc = T(0);
+          for (int c = 0; c < 4; ++c) {
+            T acc = T(0);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) acc = fma(a[s][r * 4 + q], V[c * 4 + q], acc);
-              Ln[r * 4 + c] = acc;
-            }
-          st_panel(Lb, 4 * NT, I, Ln);
-        }
-        if (I == K) {
-          T Xn[16];
+            for (int q = 0; q < 4; ++q) acc = fma(a[s][r * 4 + q], V[c * 4 + q], acc);
+            Ln[r * 4 + c] = acc;
+          }
+        st_panel(Lb, 4 * NT, tI[s], Ln);
+      }
+      if (xI[s] == K) {
+        T V[16];
+        ld16(V, Vb);
+        T Xn[16];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              T acc = T(0);
+          for (int c = 0; c < 4; ++c) {
+            T acc = T(0);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) acc = fma(V[r * 4 + q], x[s][q * 4 + c], acc);
-              Xn[r * 4 + c] = acc;
-            }
+            for (int q = 0; q < 4; ++q) acc = fma(V[r * 4 + q], x[s][q * 4 + c], acc);
+            Xn[r * 4 + c] = acc;
+          }
 #pragma unroll
-          for (int e = 0; e < 16; ++e) x[s][e] = Xn[e];
-          T XnT[16];
+        for (int e = 0; e < 16; ++e) x[s][e] = Xn[e];
+        T XnT[16];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) XnT[c * 4 + r] = Xn[r * 4 + c];
-          st_panel(Xb, 4 * NT, J, XnT);
-        }
+          for (int c = 0; c < 4; ++c) XnT[c * 4 + r] = Xn[r * 4 + c];
+        st_panel(Xb, 4 * NT, xJ[s], XnT);
       }
     }
     __syncthreads();
@@ -815,11 +926,9 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int I = tI[s], J = tJ[s];
-      if (I <= K) continue;
-      T Li[16];
-      ld_panel(Li, Lb, 4 * NT, I);
-      if (J > K) {
-        T Lj[16];
+      if (I > K && J > K) {
+        T Li[16], Lj[16];
+        ld_panel(Li, Lb, 4 * NT, I);
         ld_panel(Lj, Lb, 4 * NT, J);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -830,9 +939,12 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
             for (int q = 0; q < 4; ++q) acc = fma(-Li[r * 4 + q], Lj[c * 4 + q], acc);
             a[s][r * 4 + c] = acc;
           }
-      } else {
-        T XkT[16];   // XkT[c][q] = X_KJ[q][c]
-        ld_panel(XkT, Xb, 4 * NT, J);
+      }
+      const int XI = xI[s], XJ = xJ[s];
+      if (XI > K && XJ <= K) {
+        T Li[16], XkT[16];   // XkT[c][q] = X_KJ[q][c]
+        ld_panel(Li, Lb, 4 * NT, XI);
+        ld_panel(XkT, Xb, 4 * NT, XJ);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -847,7 +959,7 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
   }
 #pragma unroll
   for (int s = 0; s < CH; ++s) {
-    const int I = tI[s], J = tJ[s];
+    const int I = xI[s], J = xJ[s];
     if (I < 0) continue;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -905,14 +1017,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   double* dv = reinterpret_cast<double*>(sm + L.odbl);
   double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
   double *rz = nu + m, *rl = rz + n, *rn = rl + p;
+  double *qd = rn + m, *hd = qd + n, *bd = hd + p;   // q, h, b (constant over the solve)
   V* xs = reinterpret_cast<V*>(sm + L.osplit);
   T* tv = reinterpret_cast<T*>(sm + L.ovec);
   T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *dla = dl + p;
   T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p, *mdl = dsh + p, *tmp = mdl + p;
   T *dsv = tmp + p, *ccv = dsv + p;
   float* red = reinterpret_cast<float*>(sm + L.ored);
-  Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.oscr);
-  T* tscr = reinterpret_cast<T*>(sm + L.oscr);
+  Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.ocb);
+  T* tscr = reinterpret_cast<T*>(sm + L.ocb);
+  const int kscr = (int)(L.cbytes / sizeof(Acc<T>));
 
   const T* Qb = P.Q + (size_t)bi * n * n;
   const T* qb = P.q + (size_t)bi * n;
@@ -939,6 +1053,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   const float tol = (float)P.tol, mutol = (float)P.mu_tol;
   if (ok) {
     for (int i = tid; i < (m1 + p) * m1; i += NTHREADS) wSR[i] = SR[i];
+    for (int i = tid; i < n; i += NTHREADS) qd[i] = (double)qb[i];
+    for (int i = tid; i < p; i += NTHREADS) hd[i] = (double)hb[i];
+    for (int i = tid; i < m; i += NTHREADS) bd[i] = (double)bb[i];
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)qb[i]));
     for (int i = tid; i < p; i += NTHREADS) v[1] = fmaxf(v[1], fabsf((float)hb[i]));
@@ -960,9 +1077,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     for (int rs = 0; rs < 6; ++rs) {
       for (int i = tid; i < n + m; i += NTHREADS) xs[i] = Split<T>::make(i < n ? z[i] : nu[i - n]);
       __syncthreads();
-      kkt_apply<T>(n, 0, m, Qb, Gb, Ab, xs, ascr,
-                   [&](int j) { return (double)qb[j]; }, [&](int) { return 0.0; },
-                   [&](int i) { return -(double)bb[i]; }, rz, rl, rn);
+      kkt_apply<T>(n, 0, m, Qb, Gb, Ab, xs, ascr, kscr,
+                   [&](int j) { return qd[j]; }, [&](int) { return 0.0; },
+                   [&](int i) { return -bd[i]; }, rz, rl, rn);
       float v[4] = {0.f, 0.f, 0.f, 0.f};
       for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
       for (int i = tid; i < m; i += NTHREADS) v[1] = ropf<R_MAX>(v[1], fabsf((float)rn[i]));
@@ -1018,10 +1135,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
         for (int i = tid; i < n + p + m; i += NTHREADS)
           xs[i] = Split<T>::make(i < n ? z[i] : (i < n + p ? lam[i - n] : nu[i - n - p]));
         __syncthreads();
-        kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr,
-                     [&](int j) { return (double)qb[j]; },
-                     [&](int i) { return s[i] - (double)hb[i]; },
-                     [&](int i) { return -(double)bb[i]; }, rz, rl, rn);
+        kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, kscr,
+                     [&](int j) { return qd[j]; },
+                     [&](int i) { return s[i] - hd[i]; },
+                     [&](int i) { return -bd[i]; }, rz, rl, rn);
         float v[4] = {0.f, 0.f, 0.f, 0.f};
         for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
         for (int i = tid; i < p; i += NTHREADS) {
@@ -1221,7 +1338,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
     __syncthreads();
-    kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, [&](int j) { return (double)gz[j]; },
+    kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, 4 * NTHREADS, [&](int j) { return (double)gz[j]; },
                  [&](int i) { return -(s[i] / lam[i]) * dlt[i]; }, [&](int) { return 0.0; },
                  rz, rl, rn);
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
