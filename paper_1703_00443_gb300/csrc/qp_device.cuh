@@ -1359,31 +1359,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
     __syncthreads();
   }
 
-  // Gradients of Eq. 8 with d̃_λ = D(λ*) d_λ.
+  // Gradients of Eq. 8 with d̃_λ = D(λ*) d_λ, formed in the factor precision T from
+  // rounded copies of the six vectors (the outer products need no more).
+  T* vz = wv;                       // reuse: z, d_z (n each), λ, d̃_λ (p each), ν, d_ν (m each)
+  T* vdz = vz + n;
+  T* vl = y;
+  T* vdl = rhs;
+  T* vnu = u;
+  T* vdnu = u + m;
+  for (int i = tid; i < n; i += NTHREADS) { vz[i] = (T)z[i]; vdz[i] = (T)dz[i]; }
+  for (int i = tid; i < p; i += NTHREADS) { vl[i] = (T)lam[i]; vdl[i] = (T)dlt[i]; }
+  for (int i = tid; i < m; i += NTHREADS) { vnu[i] = (T)nu[i]; vdnu[i] = (T)dnu[i]; }
+  __syncthreads();
   if (P.dQ) {
     T* o = P.dQ + (size_t)bi * n * n;
     for (int e = tid; e < n * n; e += NTHREADS) {
       const int i = e / n, j = e - i * n;
-      o[e] = (T)(0.5 * (dz[i] * z[j] + z[i] * dz[j]));
+      o[e] = T(0.5) * fma(vdz[i], vz[j], vz[i] * vdz[j]);
     }
   }
-  if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[(size_t)bi * n + i] = (T)dz[i];
+  if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[(size_t)bi * n + i] = vdz[i];
   if (P.dG) {
     T* o = P.dG + (size_t)bi * p * n;
     for (int e = tid; e < p * n; e += NTHREADS) {
       const int i = e / n, j = e - i * n;
-      o[e] = (T)(dlt[i] * z[j] + lam[i] * dz[j]);
+      o[e] = fma(vdl[i], vz[j], vl[i] * vdz[j]);
     }
   }
-  if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[(size_t)bi * p + i] = (T)(-dlt[i]);
+  if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[(size_t)bi * p + i] = -vdl[i];
   if (P.dA) {
     T* o = P.dA + (size_t)bi * m * n;
     for (int e = tid; e < m * n; e += NTHREADS) {
       const int i = e / n, j = e - i * n;
-      o[e] = (T)(dnu[i] * z[j] + nu[i] * dz[j]);
+      o[e] = fma(vdnu[i], vz[j], vnu[i] * vdz[j]);
     }
   }
-  if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[(size_t)bi * m + i] = (T)(-dnu[i]);
+  if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[(size_t)bi * m + i] = -vdnu[i];
 }
 
 }  // namespace qpk
