@@ -55,18 +55,30 @@ typedef struct qp_options {
                         ‖Az−b‖∞ ≤ tol·(1+‖b‖∞) ...                                   */
   double  mu_tol;    /* ... and μ = sᵀλ/nineq ≤ mu_tol                                */
   int32_t max_iter;  /* bound on Newton steps of the interior point loop               */
-  int32_t refine;    /* FP64 iterative-refinement steps of the backward KKT solve (0-2) */
+  int32_t refine;    /* most FP64 iterative-refinement steps of the backward KKT solve
+                        (0-4): one always, more while the FP64 residual is above
+                        1e-9·(1 + ‖∂ℓ/∂z*‖∞)                                        */
+  int32_t path;      /* 0: automatic kernel choice; 1: always the global-memory kernel.
+                        Forward and backward of one batch must use the same value.      */
+  int32_t reserved;  /* set to 0                                                        */
 } qp_options;
 
-/* Default options for a dtype (QP_F32: tol 1e-10, mu_tol 1e-11, max_iter 50, refine 1;
- * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 1). */
+/* Default options for a dtype (QP_F32: tol 1e-10, mu_tol 1e-11, max_iter 50, refine 3;
+ * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 3; path 0). */
 void qp_default_options(int dtype, qp_options* opt);
 
-/* Bytes of workspace qp_forward needs for B instances of one size (0 on invalid sizes). */
+/* Bytes of workspace qp_forward needs for B instances of one size (0 on invalid sizes),
+ * for the automatic kernel choice (qp_workspace_bytes_opt: for the given options). */
 size_t qp_workspace_bytes(int dtype, int B, int n, int nineq, int neq);
+size_t qp_workspace_bytes_opt(const qp_options* opt, int dtype, int B, int n, int nineq,
+                              int neq);
 
 /* QP_OK if this build's kernels handle the size, else QP_EUNSUPPORTED / QP_EINVAL. */
 int qp_supported(int dtype, int n, int nineq, int neq);
+
+/* 1 if instances of this size run on the global-memory kernel (factors kept in the
+ * workspace, L2-resident), 0 if on the shared-memory kernel, −1 on invalid arguments. */
+int qp_uses_global_path(int dtype, int n, int nineq, int neq);
 
 /*
  * qp_forward -- batched primal-dual interior point solve (§3.1: slack form, affine
@@ -96,8 +108,8 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
  * K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z*; 0; 0; 0], then
  *   dQ = ½(d_z z*ᵀ + z* d_zᵀ), dq = d_z, dG = d̃_λ z*ᵀ + λ* d_zᵀ, dh = −d̃_λ,
  *   dA = d_ν z*ᵀ + ν* d_zᵀ,    db = −d_ν.
- * `refine` steps of iterative refinement with an FP64-accurate KKT residual follow the
- * first solve.  Q, G, A must be the same data passed to qp_forward (they feed the
+ * Up to `refine` steps of iterative refinement with an FP64-accurate KKT residual follow
+ * the first solve (see qp_options).  Q, G, A must be the same data passed to qp_forward (they feed the
  * refinement residual).  dl_dz [B,n] is ∂ℓ/∂z*.  Any gradient pointer may be NULL
  * (not wanted).  Instances whose forward status was NOT_PD or NUMERICAL get NaN
  * gradients.

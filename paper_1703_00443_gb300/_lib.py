@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqp_gb300.so")
 
 UNITS = ["qp_abi", "qp_fwd_f32", "qp_fwd_f64", "qp_bwd"]
-HEADERS = ["qp_device.cuh", "qp_launch.cuh"]
+HEADERS = ["qp_device.cuh", "qp_launch.cuh", "qp_large.cuh"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-Xptxas", "-v"]
@@ -76,13 +76,16 @@ c_int, c_size_t, c_void_p, c_double = ctypes.c_int, ctypes.c_size_t, ctypes.c_vo
 
 class QPOptions(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("mu_tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int32), ("refine", ctypes.c_int32)]
+                ("max_iter", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 EXPORTS = {
     "qp_default_options": (None, [c_int, ctypes.POINTER(QPOptions)]),
     "qp_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
+    "qp_workspace_bytes_opt": (c_size_t, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]),
     "qp_supported": (c_int, [c_int, c_int, c_int, c_int]),
+    "qp_uses_global_path": (c_int, [c_int, c_int, c_int, c_int]),
     "qp_forward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                    + [c_void_p] * 13 + [c_size_t, c_void_p]),
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]

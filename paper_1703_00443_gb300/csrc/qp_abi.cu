@@ -51,32 +51,59 @@ bool pick_variant(int dtype, int n, int nineq, int neq, int* SW, int* CH) {
   return false;
 }
 
-size_t fwd_smem(int dtype, int n, int nineq, int neq) {
+size_t fwd_smem(int dtype, int n, int nz, int nineq, int neq, bool large) {
   if (dtype == QP_F32) {
     qpk::FwdSmem<float> L;
-    L.init(n, nineq, neq);
+    L.init(n, nz, nineq, neq, large);
     return L.total;
   }
   qpk::FwdSmem<double> L;
-  L.init(n, nineq, neq);
+  L.init(n, nz, nineq, neq, large);
   return L.total;
 }
 
-size_t bwd_smem(int dtype, int n, int nineq, int neq) {
+size_t bwd_smem(int dtype, int n, int nz, int nineq, int neq) {
   if (dtype == QP_F32) {
     qpk::BwdSmem<float> L;
-    L.init(n, nineq, neq);
+    L.init(n, nz, nineq, neq);
     return L.total;
   }
   qpk::BwdSmem<double> L;
-  L.init(n, nineq, neq);
+  L.init(n, nz, nineq, neq);
   return L.total;
 }
 
-size_t ws_inst(int dtype, int n, int nineq, int neq) {
+// Kernel path for a size: the shared-memory kernel when a register-tile variant covers it and
+// its factors fit in shared memory, else the global-memory kernel.  A pure function of the
+// sizes and the device's shared-memory limit, so forward and backward always agree.
+struct Plan {
+  bool ok = false, large = false;
+  int sw = 0, ch = 0, nz = 0;
+  size_t fsmem = 0, bsmem = 0, ws = 0;
+};
+
+Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
+  Plan pl;
+  const size_t lim = (size_t)max_smem_optin();
+  int sw = 0, ch = 0;
+  const int nz4 = qpk::padded_nz(n, neq);
+  if (!force_global && pick_variant(dtype, n, nineq, neq, &sw, &ch) &&
+      fwd_smem(dtype, n, nz4, nineq, neq, false) <= lim) {
+    pl.large = false;
+    pl.sw = sw;
+    pl.ch = ch;
+    pl.nz = nz4;
+  } else {
+    pl.large = true;
+    pl.nz = n + ((qpk::LNB - (n + neq) % qpk::LNB) % qpk::LNB);
+  }
+  pl.fsmem = fwd_smem(dtype, n, pl.nz, nineq, neq, pl.large);
+  pl.bsmem = bwd_smem(dtype, n, pl.nz, nineq, neq);
   qpk::WsLayout W;
-  W.init(n, nineq, neq, dtype == QP_F32 ? 4 : 8);
-  return W.inst;
+  W.init(n, pl.nz, nineq, neq, dtype == QP_F32 ? 4 : 8, pl.large);
+  pl.ws = W.inst;
+  pl.ok = pl.fsmem <= lim && pl.bsmem <= lim;
+  return pl;
 }
 
 }  // namespace
@@ -101,21 +128,30 @@ void qp_default_options(int dtype, qp_options* opt) {
     opt->mu_tol = 1e-11;
     opt->max_iter = 50;
   }
-  opt->refine = 1;
+  opt->refine = 3;
+  opt->path = 0;
+  opt->reserved = 0;
 }
 
 size_t qp_workspace_bytes(int dtype, int B, int n, int nineq, int neq) {
   if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return 0;
-  return (size_t)B * ws_inst(dtype, n, nineq, neq);
+  return (size_t)B * make_plan(dtype, n, nineq, neq).ws;
+}
+
+size_t qp_workspace_bytes_opt(const qp_options* opt, int dtype, int B, int n, int nineq,
+                              int neq) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return 0;
+  return (size_t)B * make_plan(dtype, n, nineq, neq, opt ? opt->path : 0).ws;
 }
 
 int qp_supported(int dtype, int n, int nineq, int neq) {
   if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(1, n, nineq, neq)) return QP_EINVAL;
-  int sw, ch;
-  if (!pick_variant(dtype, n, nineq, neq, &sw, &ch)) return QP_EUNSUPPORTED;
-  if (fwd_smem(dtype, n, nineq, neq) > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
-  if (bwd_smem(dtype, n, nineq, neq) > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
-  return QP_OK;
+  return make_plan(dtype, n, nineq, neq).ok ? QP_OK : QP_EUNSUPPORTED;
+}
+
+int qp_uses_global_path(int dtype, int n, int nineq, int neq) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(1, n, nineq, neq)) return -1;
+  return make_plan(dtype, n, nineq, neq).large ? 1 : 0;
 }
 
 int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
@@ -128,30 +164,30 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
   if (nineq > 0 && (!G || !h)) return QP_EINVAL;
   if (neq > 0 && (!A || !b)) return QP_EINVAL;
   if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
-  if (workspace_bytes < qp_workspace_bytes(dtype, B, n, nineq, neq)) return QP_ENOSPACE;
-  int sw = 0, ch = 0;
-  if (!pick_variant(dtype, n, nineq, neq, &sw, &ch)) return QP_EUNSUPPORTED;
-  const size_t smem = fwd_smem(dtype, n, nineq, neq);
-  if (smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
   qp_options o;
   if (opt) o = *opt; else qp_default_options(dtype, &o);
-  if (o.max_iter < 0) return QP_EINVAL;
+  if (o.max_iter < 0 || o.path < 0 || o.path > 1) return QP_EINVAL;
+  const Plan pl = make_plan(dtype, n, nineq, neq, o.path);
+  if (workspace_bytes < (size_t)B * pl.ws) return QP_ENOSPACE;
+  if (!pl.ok) return QP_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (dtype == QP_F32) {
-    qpk::FwdParams<float> P{B, n, nineq, neq,
+    qpk::FwdParams<float> P{B, n, nineq, neq, pl.nz,
                             (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
                             (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
                             status, iters, resid, (unsigned char*)workspace,
-                            ws_inst(dtype, n, nineq, neq), o.tol, o.mu_tol, o.max_iter};
-    e = qpk::launch_fwd_f32(P, sw, ch, smem, st);
+                            pl.ws, o.tol, o.mu_tol, o.max_iter};
+    e = pl.large ? qpk::launch_fwd_large_f32(P, pl.fsmem, st)
+                 : qpk::launch_fwd_f32(P, pl.sw, pl.ch, pl.fsmem, st);
   } else {
-    qpk::FwdParams<double> P{B, n, nineq, neq,
+    qpk::FwdParams<double> P{B, n, nineq, neq, pl.nz,
                              (const double*)Q, (const double*)q, (const double*)G, (const double*)h,
                              (const double*)A, (const double*)b, (double*)z, (double*)lam,
                              (double*)nu, status, iters, resid, (unsigned char*)workspace,
-                             ws_inst(dtype, n, nineq, neq), o.tol, o.mu_tol, o.max_iter};
-    e = qpk::launch_fwd_f64(P, sw, ch, smem, st);
+                             pl.ws, o.tol, o.mu_tol, o.max_iter};
+    e = pl.large ? qpk::launch_fwd_large_f64(P, pl.fsmem, st)
+                 : qpk::launch_fwd_f64(P, pl.sw, pl.ch, pl.fsmem, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;
 }
@@ -166,26 +202,28 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
   if (nineq > 0 && !G) return QP_EINVAL;
   if (neq > 0 && !A) return QP_EINVAL;
   if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
-  if (workspace_bytes < qp_workspace_bytes(dtype, B, n, nineq, neq)) return QP_ENOSPACE;
-  const size_t smem = bwd_smem(dtype, n, nineq, neq);
-  if (smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
   qp_options o;
   if (opt) o = *opt; else qp_default_options(dtype, &o);
-  if (o.refine < 0 || o.refine > 4) return QP_EINVAL;
+  if (o.refine < 0 || o.refine > 4 || o.path < 0 || o.path > 1) return QP_EINVAL;
+  const Plan pl = make_plan(dtype, n, nineq, neq, o.path);
+  if (workspace_bytes < (size_t)B * pl.ws) return QP_ENOSPACE;
+  if (!pl.ok) return QP_EUNSUPPORTED;
+  const size_t smem = pl.bsmem;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (dtype == QP_F32) {
-    qpk::BwdParams<float> P{B, n, nineq, neq, (const float*)Q, (const float*)G, (const float*)A,
+    qpk::BwdParams<float> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0,
+                            (const float*)Q, (const float*)G, (const float*)A,
                             (const float*)dl_dz, (float*)dQ, (float*)dq, (float*)dG, (float*)dh,
                             (float*)dA, (float*)db, (const unsigned char*)workspace,
-                            ws_inst(dtype, n, nineq, neq), o.refine};
+                            pl.ws, o.refine};
     e = qpk::launch_bwd_f32(P, smem, st);
   } else {
-    qpk::BwdParams<double> P{B, n, nineq, neq, (const double*)Q, (const double*)G,
+    qpk::BwdParams<double> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0,
+                             (const double*)Q, (const double*)G,
                              (const double*)A, (const double*)dl_dz, (double*)dQ, (double*)dq,
                              (double*)dG, (double*)dh, (double*)dA, (double*)db,
-                             (const unsigned char*)workspace, ws_inst(dtype, n, nineq, neq),
-                             o.refine};
+                             (const unsigned char*)workspace, pl.ws, o.refine};
     e = qpk::launch_bwd_f64(P, smem, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;

@@ -48,15 +48,27 @@ __host__ __device__ inline int padded_nz(int n, int m) { return n + ((4 - (n + m
 
 // ------------------------------------------------------------------ layouts
 // Per-instance workspace (global memory) kept from forward to backward.
+// Layout shared by both kernel paths (the backward pass reads only this prefix):
+// SR = [S; RE] ((m1+p) × m1, m1 = nz + neq), the p×p block with X = L⁻¹ (lower) and M
+// (strict upper), the FP64 iterate (z, s, λ, ν) and the status word.  The global-memory
+// path appends diag(M), its Cholesky work matrix and its panel scratch.
 struct WsLayout {
-  size_t oSR, oX, oIt, oSt, inst;
-  __host__ __device__ void init(int n, int p, int m, int esz) {
-    const size_t m1 = (size_t)padded_nz(n, m) + m;
+  size_t oSR, oX, oIt, oSt, odM, oAw, oPan, inst;
+  __host__ __device__ void init(int n, int nz, int p, int m, int esz, bool large) {
+    const size_t m1 = (size_t)nz + m;
     oSR = 0;
     oX = align_up(oSR + (m1 + p) * m1 * esz, 256);
     oIt = align_up(oX + (size_t)p * p * esz, 256);
     oSt = align_up(oIt + 8 * ((size_t)n + 2 * (size_t)p + m), 256);
-    inst = align_up(oSt + 16, 256);
+    size_t o = align_up(oSt + 16, 256);
+    odM = oAw = oPan = o;
+    if (large) {
+      const size_t N = m1 + p, ldp = (N + 3) / 4 * 4;
+      odM = o;  o = align_up(o + (size_t)p * esz, 256);
+      oAw = o;  o = align_up(o + (size_t)p * p * esz, 256);
+      oPan = o; o = align_up(o + 2 * 16 * ldp * esz, 256);
+    }
+    inst = o;
   }
 };
 
@@ -65,8 +77,10 @@ template <typename T>
 struct FwdSmem {
   int nz, m1, N3, ldS, ldM, NT3, NTp;
   size_t oSR, oMb, odM, ocb, cbytes, odbl, osplit, ovec, ored, total;
-  __host__ __device__ void init(int n, int p, int m) {
-    nz = padded_nz(n, m);
+  // large: S/RE, M/X and diag(M) live in the global workspace, only vectors and a work
+  // region stay in shared memory.
+  __host__ __device__ void init(int n, int nzp, int p, int m, bool large) {
+    nz = nzp;
     m1 = nz + m;
     N3 = m1 + p;
     ldS = m1;
@@ -75,16 +89,24 @@ struct FwdSmem {
     NTp = (p + 3) / 4;
     const size_t es = sizeof(T);
     size_t o = 0;
-    oSR = o;   o = align_up(o + (size_t)(m1 + p) * ldS * es, 16);
-    oMb = o;   o = align_up(o + (size_t)p * ldM * es, 16);
-    odM = o;   o = align_up(o + (size_t)p * es, 16);
-    // Work region: panel buffers of the blocked factorisations (sweep_setup, chol_inv),
-    // reused as partial-sum scratch by kkt_apply and mv_cols (never live at the same time).
+    oSR = oMb = odM = 0;
+    if (!large) {
+      oSR = o;   o = align_up(o + (size_t)(m1 + p) * ldS * es, 16);
+      oMb = o;   o = align_up(o + (size_t)p * ldM * es, 16);
+      odM = o;   o = align_up(o + (size_t)p * es, 16);
+    }
+    // Work region: panel buffers of the blocked factorisations, reused as partial-sum
+    // scratch by kkt_apply and mv_cols (never live at the same time).
     ocb = o;
     {
-      size_t a = 2 * (32 * (size_t)NT3 + 16), b = 2 * (32 * (size_t)NTp + 16);
-      size_t c = (a > b ? a : b) * es + 64;
-      if (c < 8 * (size_t)NTHREADS) c = 8 * (size_t)NTHREADS;
+      size_t c;
+      if (!large) {
+        size_t a = 2 * (32 * (size_t)NT3 + 16), b = 2 * (32 * (size_t)NTp + 16);
+        c = (a > b ? a : b) * es + 64;
+        if (c < 8 * (size_t)NTHREADS) c = 8 * (size_t)NTHREADS;
+      } else {
+        c = 8 * (size_t)4 * NTHREADS;   // ≥ (2·16·16 + 16) elements of T as well
+      }
       cbytes = align_up(c, 16);
       o += cbytes;
     }
@@ -100,8 +122,8 @@ struct FwdSmem {
 template <typename T>
 struct BwdSmem {
   size_t odbl, osplit, ovec, ored, oscr, total;
-  __host__ __device__ void init(int n, int p, int m) {
-    const size_t m1 = (size_t)padded_nz(n, m) + m, es = sizeof(T);
+  __host__ __device__ void init(int n, int nz, int p, int m) {
+    const size_t m1 = (size_t)nz + m, es = sizeof(T);
     size_t o = 0;
     odbl = o;   o = align_up(o + 8 * (3 * ((size_t)n + p + m) + 2 * (size_t)p), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
@@ -114,7 +136,7 @@ struct BwdSmem {
 
 template <typename T>
 struct FwdParams {
-  int B, n, p, m;
+  int B, n, p, m, nz;
   const T *Q, *q, *G, *h, *A, *b;
   T *z, *lam, *nu;
   int32_t *status, *iters;
@@ -127,7 +149,8 @@ struct FwdParams {
 
 template <typename T>
 struct BwdParams {
-  int B, n, p, m;
+  int B, n, p, m, nz;
+  int large;
   const T *Q, *G, *A, *dl_dz;
   T *dQ, *dq, *dG, *dh, *dA, *db;
   const unsigned char* ws;
@@ -1000,19 +1023,27 @@ template <> __device__ __forceinline__ double ratio_to<double>(double r) {
   return fmin(fmax(r, 1e-300), 1e300);
 }
 
-// ------------------------------------------------------------------ forward kernel
-template <typename T, int SW, int CH>
-__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> P) {
+}  // namespace qpk
+
+#include "qp_large.cuh"
+
+namespace qpk {
+
+// ------------------------------------------------------------------ forward kernels
+// Body of the forward pass for one instance (one 512-thread block), shared by the
+// shared-memory kernel and the global-memory kernel.  SR (= [S; RE], leading dimension
+// ldS = m1), Mb (M strict upper / X lower, leading dimension ldM) and dM point to shared or
+// global memory; setup() fills them (the setup sweep) and factor(dsh) factors
+// M + D(dsh) into X.  With ws_resident the factors already live in the workspace, otherwise
+// they are copied there for the backward pass.
+template <typename T, typename FS, typename FF>
+__device__ __forceinline__ void fwd_body(const FwdParams<T>& P, const FwdSmem<T>& L,
+                                         unsigned char* sm, T* SR, T* Mb, T* dM,
+                                         bool ws_resident, FS setup, FF factor) {
   using V = typename Split<T>::V;
-  extern __shared__ __align__(16) unsigned char sm[];
   const int bi = blockIdx.x, tid = threadIdx.x;
   const int n = P.n, p = P.p, m = P.m;
-  FwdSmem<T> L;
-  L.init(n, p, m);
   const int m1 = L.m1, nz = L.nz;
-  T* SR = reinterpret_cast<T*>(sm + L.oSR);
-  T* Mb = reinterpret_cast<T*>(sm + L.oMb);
-  T* dM = reinterpret_cast<T*>(sm + L.odM);
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
   double* dv = reinterpret_cast<double*>(sm + L.odbl);
   double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
@@ -1027,6 +1058,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.ocb);
   T* tscr = reinterpret_cast<T*>(sm + L.ocb);
   const int kscr = (int)(L.cbytes / sizeof(Acc<T>));
+  (void)cb;
 
   const T* Qb = P.Q + (size_t)bi * n * n;
   const T* qb = P.q + (size_t)bi * n;
@@ -1035,16 +1067,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   const T* Ab = m ? P.A + (size_t)bi * m * n : nullptr;
   const T* bb = m ? P.b + (size_t)bi * m : nullptr;
   WsLayout W;
-  W.init(n, p, m, (int)sizeof(T));
+  W.init(n, nz, p, m, (int)sizeof(T), ws_resident);
   unsigned char* wsb = P.ws + (size_t)bi * P.ws_inst;
   T* wSR = reinterpret_cast<T*>(wsb + W.oSR);
   T* wX = reinterpret_cast<T*>(wsb + W.oX);
   double* wIt = reinterpret_cast<double*>(wsb + W.oIt);
   int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
+  const int ldS = m1, ldM = p > 0 ? p : 1;
 
   int status = ST_CONV, it = 0;
   float last[4] = {0.f, 0.f, 0.f, 0.f};   // residual norms and μ at the returned iterate
-  bool ok = sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
+  bool ok = setup(Qb, Ab, Gb);
   __syncthreads();
   if (!ok) status = ST_NOTPD;
 
@@ -1052,7 +1085,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   float tz = 0.f, tl = 0.f, tn = 0.f;
   const float tol = (float)P.tol, mutol = (float)P.mu_tol;
   if (ok) {
-    for (int i = tid; i < (m1 + p) * m1; i += NTHREADS) wSR[i] = SR[i];
+    if (!ws_resident)
+      for (int i = tid; i < (m1 + p) * m1; i += NTHREADS) wSR[i] = SR[i];
     for (int i = tid; i < n; i += NTHREADS) qd[i] = (double)qb[i];
     for (int i = tid; i < p; i += NTHREADS) hd[i] = (double)hb[i];
     for (int i = tid; i < m; i += NTHREADS) bd[i] = (double)bb[i];
@@ -1070,7 +1104,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     // Equality-constrained QP: [z; ν] = S·[−q; b], then FP64-residual refinement.
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : (i < nz ? T(0) : bb[i - nz]);
     __syncthreads();
-    mv_rows<8>(SR, L.ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
+    mv_rows<8>(SR, ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
       if (r < n) z[r] = (double)val; else if (r >= nz) nu[r - nz] = (double)val;
     });
     __syncthreads();
@@ -1090,7 +1124,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
       if (v[0] <= 0.01f * tz && v[1] <= 0.01f * tn) break;
       for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
       __syncthreads();
-      mv_rows<8>(SR, L.ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
+      mv_rows<8>(SR, ldS, m1, m1, TRI_ALL, u, [&](int r, T val) {
         if (r < n) z[r] += (double)val; else if (r >= nz) nu[r - nz] += (double)val;
       });
       __syncthreads();
@@ -1100,15 +1134,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     for (int i = tid; i < p; i += NTHREADS) dsh[i] = T(1);
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -qb[i] : (i < nz ? T(0) : bb[i - nz]);
     __syncthreads();
-    ok = chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb);
+    ok = factor(dsh);
     if (!ok) status = ST_NOTPD;
     if (ok) {
-      mv_rows<8>(SR, L.ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
+      mv_rows<8>(SR, ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
       __syncthreads();
       for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] - hb[i];
       __syncthreads();
-      chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
-      mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, TRI_ALL, dl, tscr,
+      chol_solve(p, Mb, ldM, rhs, y, dl, tscr);
+      mv_cols(SR + (size_t)m1 * ldS, ldS, p, m1, TRI_ALL, dl, tscr,
               [&](int c, T val) { dzn[c] = wv[c] - val; });
       float v[4] = {-INFINITY, 0.f, -INFINITY, 0.f};
       for (int i = tid; i < n; i += NTHREADS) z[i] = (double)dzn[i];
@@ -1167,17 +1201,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
         for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>((T)s[i] / (T)lam[i]);
         for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
         __syncthreads();
-        if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) {
+        if (!factor(dsh)) {
           status = ST_NOTPD;
           break;
         }
         // Affine-scaling (predictor) direction, Eq. 9.
-        mv_rows<8>(SR, L.ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
+        mv_rows<8>(SR, ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
         __syncthreads();
         for (int i = tid; i < p; i += NTHREADS) rhsa[i] = wv[m1 + i] + (T)(rl[i] - s[i]);
         __syncthreads();
-        chol_solve(p, Mb, L.ldM, rhsa, y, dla, tscr);
-        mv_sym_upper(p, Mb, L.ldM, dM, dla, tmp, mdl, tscr);
+        chol_solve(p, Mb, ldM, rhsa, y, dla, tscr);
+        mv_sym_upper(p, Mb, ldM, dM, dla, tmp, mdl, tscr);
         // Δs from the complementarity row where s ≤ λ and from the primal row
         // GΔz + Δs = −r_λ (with GΔz = RE·u − MΔλ) elsewhere: the first multiplies the
         // FP32 error of Δλ by s/λ, which is large exactly where the second is safe.
@@ -1207,10 +1241,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
           rhs[i] = rhsa[i] + cc / (T)lam[i];
         }
         __syncthreads();
-        chol_solve(p, Mb, L.ldM, rhs, y, dl, tscr);
-        mv_cols(SR + (size_t)m1 * L.ldS, L.ldS, p, m1, TRI_ALL, dl, tscr,
+        chol_solve(p, Mb, ldM, rhs, y, dl, tscr);
+        mv_cols(SR + (size_t)m1 * ldS, ldS, p, m1, TRI_ALL, dl, tscr,
                 [&](int c, T val) { dzn[c] = wv[c] - val; });
-        mv_sym_upper(p, Mb, L.ldM, dM, dl, tmp, mdl, tscr);
+        mv_sym_upper(p, Mb, ldM, dM, dl, tmp, mdl, tscr);
         float w6[4] = {INFINITY, 0.f, 0.f, 0.f};
         for (int i = tid; i < p; i += NTHREADS) {
           const T si = (T)s[i], li = (T)lam[i], d = dl[i];
@@ -1234,7 +1268,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
       if (status == ST_CONV || status == ST_MAXIT) {
         for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>((T)s[i] / (T)lam[i]);
         __syncthreads();
-        if (!chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb)) status = ST_NOTPD;
+        if (!factor(dsh)) status = ST_NOTPD;
       }
     }
   }
@@ -1258,7 +1292,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
     if (P.nu) P.nu[(size_t)bi * m + i] = (T)v;
     wIt[n + 2 * p + i] = v;
   }
-  if (!bad)
+  if (!bad && !ws_resident)
     for (int i = tid; i < p * p; i += NTHREADS) wX[i] = Mb[i];
   if (tid == 0) {
     wSt[0] = status;
@@ -1273,15 +1307,57 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
   }
 }
 
+
+// Shared-memory kernel: S/RE and M/X held in shared memory, register-tile factorisations.
+template <typename T, int SW, int CH>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  FwdSmem<T> L;
+  L.init(P.n, P.nz, P.p, P.m, false);
+  T* SR = reinterpret_cast<T*>(sm + L.oSR);
+  T* Mb = reinterpret_cast<T*>(sm + L.oMb);
+  T* dM = reinterpret_cast<T*>(sm + L.odM);
+  T* cb = reinterpret_cast<T*>(sm + L.ocb);
+  const int n = P.n, p = P.p, m = P.m;
+  fwd_body<T>(P, L, sm, SR, Mb, dM, false,
+      [&](const T* Qb, const T* Ab, const T* Gb) {
+        return sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
+      },
+      [&](const T* dsh) { return chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb); });
+}
+
+// Global-memory kernel: the factors live in the instance's workspace (see qp_large.cuh).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_large_kernel(const FwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  FwdSmem<T> L;
+  L.init(P.n, P.nz, P.p, P.m, true);
+  const int n = P.n, p = P.p, m = P.m, nz = P.nz;
+  WsLayout W;
+  W.init(n, nz, p, m, (int)sizeof(T), true);
+  unsigned char* wsb = P.ws + (size_t)blockIdx.x * P.ws_inst;
+  T* SR = reinterpret_cast<T*>(wsb + W.oSR);
+  T* Mb = reinterpret_cast<T*>(wsb + W.oX);
+  T* dM = reinterpret_cast<T*>(wsb + W.odM);
+  T* Aw = reinterpret_cast<T*>(wsb + W.oAw);
+  T* pan = reinterpret_cast<T*>(wsb + W.oPan);
+  T* cb = reinterpret_cast<T*>(sm + L.ocb);
+  fwd_body<T>(P, L, sm, SR, Mb, dM, true,
+      [&](const T* Qb, const T* Ab, const T* Gb) {
+        return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, cb);
+      },
+      [&](const T* dsh) { return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, cb); });
+}
+
 // ------------------------------------------------------------------ backward kernel
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> P) {
   using V = typename Split<T>::V;
   extern __shared__ __align__(16) unsigned char sm[];
   const int bi = blockIdx.x, tid = threadIdx.x;
-  const int n = P.n, p = P.p, m = P.m, nz = padded_nz(n, m), m1 = nz + m;
+  const int n = P.n, p = P.p, m = P.m, nz = P.nz, m1 = nz + m;
   BwdSmem<T> L;
-  L.init(n, p, m);
+  L.init(n, nz, p, m);
   double* dv = reinterpret_cast<double*>(sm + L.odbl);
   double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
   double *dz = nu + m, *dlt = dz + n, *dnu = dlt + p;
@@ -1291,9 +1367,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *rhs = dl + p;
   Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.oscr);
   T* tscr = reinterpret_cast<T*>(sm + L.oscr);
+  float* red = reinterpret_cast<float*>(sm + L.ored);
 
   WsLayout W;
-  W.init(n, p, m, (int)sizeof(T));
+  W.init(n, nz, p, m, (int)sizeof(T), P.large != 0);
   const unsigned char* wsb = P.ws + (size_t)bi * P.ws_inst;
   const T* SR = reinterpret_cast<const T*>(wsb + W.oSR);
   const T* X = reinterpret_cast<const T*>(wsb + W.oX);
@@ -1333,7 +1410,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   __syncthreads();
 
   // Iterative refinement with the FP64-accurate residual of the reduced system
-  //   ρ_z = Q d_z + Gᵀ d̃_λ + Aᵀ d_ν + ∂ℓ/∂z,  ρ_λ = G d_z − D(s/λ) d̃_λ,  ρ_ν = A d_z.
+  //   ρ_z = Q d_z + Gᵀ d̃_λ + Aᵀ d_ν + ∂ℓ/∂z,  ρ_λ = G d_z − D(s/λ) d̃_λ,  ρ_ν = A d_z:
+  // at least one correction, then further ones (at most P.refine in all) while
+  // ‖ρ‖∞ > 1e-9·(1 + ‖∂ℓ/∂z‖∞).  Ill-conditioned equality blocks (A Q⁻¹ Aᵀ near singular)
+  // need the extra steps; well-conditioned ones stop after the first.
+  float gmax;
+  {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)gz[i]));
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
+    gmax = v[0];
+  }
+  const float rthr = 1e-9f * (1.f + gmax);
   for (int rs = 0; rs < P.refine; ++rs) {
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
@@ -1341,6 +1429,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
     kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, 4 * NTHREADS, [&](int j) { return (double)gz[j]; },
                  [&](int i) { return -(s[i] / lam[i]) * dlt[i]; }, [&](int) { return 0.0; },
                  rz, rl, rn);
+    if (rs > 0) {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
+      for (int i = tid; i < p; i += NTHREADS) v[1] = ropf<R_MAX>(v[1], fabsf((float)rl[i]));
+      for (int i = tid; i < m; i += NTHREADS) v[2] = ropf<R_MAX>(v[2], fabsf((float)rn[i]));
+      block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
+      if (v[0] <= rthr && v[1] <= rthr && v[2] <= rthr) break;
+    }
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
     __syncthreads();
     mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });

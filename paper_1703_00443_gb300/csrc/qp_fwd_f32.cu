@@ -20,4 +20,12 @@ cudaError_t launch_fwd_f32(const FwdParams<float>& P, int SW, int CH, size_t sme
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_fwd_large_f32(const FwdParams<float>& P, size_t smem, cudaStream_t st) {
+  auto k = qp_fwd_large_kernel<float>;
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<P.B, NTHREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
 }  // namespace qpk

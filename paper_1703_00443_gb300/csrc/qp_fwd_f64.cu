@@ -18,4 +18,12 @@ cudaError_t launch_fwd_f64(const FwdParams<double>& P, int SW, int CH, size_t sm
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_fwd_large_f64(const FwdParams<double>& P, size_t smem, cudaStream_t st) {
+  auto k = qp_fwd_large_kernel<double>;
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<P.B, NTHREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
 }  // namespace qpk

@@ -14,6 +14,8 @@ bool fwd_variant_exists(int esz, int SW, int CH);
 
 cudaError_t launch_fwd_f32(const FwdParams<float>& P, int SW, int CH, size_t smem, cudaStream_t st);
 cudaError_t launch_fwd_f64(const FwdParams<double>& P, int SW, int CH, size_t smem, cudaStream_t st);
+cudaError_t launch_fwd_large_f32(const FwdParams<float>& P, size_t smem, cudaStream_t st);
+cudaError_t launch_fwd_large_f64(const FwdParams<double>& P, size_t smem, cudaStream_t st);
 cudaError_t launch_bwd_f32(const BwdParams<float>& P, size_t smem, cudaStream_t st);
 cudaError_t launch_bwd_f64(const BwdParams<double>& P, size_t smem, cudaStream_t st);
 

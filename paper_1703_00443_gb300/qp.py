@@ -104,9 +104,20 @@ class ForwardResult:
     options: _lib.QPOptions
 
 
-def alloc_workspace(dtype, B, n, nineq, neq, device) -> torch.Tensor:
-    nbytes = max(workspace_bytes(dtype, B, n, nineq, neq), 256)
-    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+def alloc_workspace(dtype, B, n, nineq, neq, device, options=None) -> torch.Tensor:
+    if options is None:
+        nbytes = workspace_bytes(dtype, B, n, nineq, neq)
+    else:
+        lib = _lib.load()
+        nbytes = int(lib.qp_workspace_bytes_opt(ctypes.byref(options),
+                                                QP_F32 if dtype == torch.float32 else QP_F64,
+                                                B, n, nineq, neq))
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def uses_global_path(dtype, n, nineq, neq) -> bool:
+    lib = _lib.load()
+    return lib.qp_uses_global_path(QP_F32 if dtype == torch.float32 else QP_F64, n, nineq, neq) == 1
 
 
 def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=None,
@@ -119,7 +130,7 @@ def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=
     lib = _lib.load()
     opts = options if options is not None else default_options(dt)
     if workspace is None:
-        workspace = alloc_workspace(dt, B, n, nineq, neq, dev)
+        workspace = alloc_workspace(dt, B, n, nineq, neq, dev, opts)
     if out is None:
         z = torch.empty((B, n), device=dev, dtype=dt)
         lam = torch.empty((B, nineq), device=dev, dtype=dt)

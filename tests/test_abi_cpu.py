@@ -28,7 +28,7 @@ def test_host_side_queries():
     lib = _lib.load()
     o = _lib.QPOptions()
     lib.qp_default_options(0, ctypes.byref(o))
-    assert o.max_iter == 50 and o.refine == 1 and 0 < o.tol < 1e-6
+    assert o.max_iter == 50 and o.refine == 3 and o.path == 0 and 0 < o.tol < 1e-6
     lib.qp_default_options(1, ctypes.byref(o))
     assert o.max_iter == 100 and o.tol <= 1e-12
     assert lib.qp_workspace_bytes(0, 128, 100, 100, 50) >= 128 * (250 * 150 + 100 * 100) * 4
@@ -38,6 +38,11 @@ def test_host_side_queries():
     assert lib.qp_supported(1, 10, 20, 0) == 0
     assert lib.qp_supported(0, 10, 5, 11) == 1      # more equalities than variables
     assert lib.qp_strerror(0) == b"ok"
+    # sizes beyond shared memory run on the global-memory kernel
+    assert lib.qp_uses_global_path(0, 100, 100, 50) == 0
+    assert lib.qp_uses_global_path(0, 500, 500, 250) == 1
+    assert lib.qp_supported(0, 500, 500, 250) == 0
+    assert lib.qp_supported(0, 256, 512, 64) == 0
 
 
 def test_invalid_arguments_rejected_before_launch():

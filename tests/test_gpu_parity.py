@@ -151,3 +151,46 @@ def test_instance_alone_equals_in_batch_and_deterministic():
     for k in ("z", "lam", "nu") + GRAD_NAMES:
         assert np.array_equal(full[k], again[k]), k
         assert np.array_equal(full[k][9:10], alone[k]), k
+
+
+def _run_opts(batch, g, dtype, options):
+    T = _to_dev(batch, dtype)
+    fwd = qp_forward(*T, options=options)
+    grads = qp_backward(fwd, torch.from_numpy(np.ascontiguousarray(g)).to(T[0].device, T[0].dtype))
+    torch.cuda.synchronize()
+    out = dict(z=fwd.z.cpu().double().numpy(), lam=fwd.lam.cpu().double().numpy(),
+               nu=fwd.nu.cpu().double().numpy(), status=fwd.status.cpu().numpy())
+    for k, v in zip(GRAD_NAMES, grads):
+        out[k] = v.cpu().double().numpy()
+    return out
+
+
+@pytest.mark.parametrize("n,nineq,neq", [(7, 13, 3), (33, 9, 0), (12, 0, 5), (50, 50, 25),
+                                         (20, 37, 19)])
+def test_global_memory_kernel_small_sizes(n, nineq, neq):
+    """The global-memory kernel (forced) on sizes the oracle checks quickly, including
+    padding of n + neq to the 16-pivot blocks and a partial last Cholesky block."""
+    from paper_1703_00443_gb300 import default_options
+    opts = default_options(torch.float32)
+    opts.path = 1
+    B = 4
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_PLAIN, dtype=np.float32,
+                                start=2000)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PLAIN, start=2000)
+    out = _run_opts(batch, g, np.float32, opts)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
+
+
+@pytest.mark.parametrize("n,nineq,neq", [(500, 500, 250), (256, 512, 64)])
+def test_global_memory_kernel_large_sizes(n, nineq, neq):
+    """Sizes whose factors exceed shared memory: the timing sweep's n = 500 point and the
+    largest instance shape of the uneven workload."""
+    from paper_1703_00443_gb300.qp import uses_global_path
+    assert uses_global_path(torch.float32, n, nineq, neq)
+    B = 2
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_SWEEP, dtype=np.float32)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
+    out = _run(batch, g, np.float32)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
