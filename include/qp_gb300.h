@@ -119,6 +119,58 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                 const void* workspace, size_t workspace_bytes, const void* dl_dz,
                 void* dQ, void* dq, void* dG, void* dh, void* dA, void* db, void* stream);
 
+/*
+ * Packed batches of uneven sizes (one persistent launch each way).
+ *
+ * Instance i has its own (n_i, nineq_i, neq_i); its data are packed back to back in index
+ * order in each input buffer (Q_i n_i×n_i row-major, then Q_{i+1}, ...; likewise q, G, h, A,
+ * b, the outputs z, λ, ν and the gradients, which share the inputs' offsets).  The
+ * paper's solver is stated for fixed-size batches (§3.1); this entry runs the same method
+ * per instance, each on the kernel path its own size selects, so an instance's result does
+ * not depend on the rest of the batch.
+ */
+typedef struct qp_instance_desc {
+  int32_t n, nineq, neq;     /* sizes                                                   */
+  int32_t id;                /* index of the instance (status/iters/resid slots)        */
+  int32_t nz;                /* n plus dummy padding (set by qp_packed_plan)            */
+  int32_t flags;             /* bit 0: global-memory kernel (set by qp_packed_plan)     */
+  int64_t oQ, oq, oG, oh, oA, ob;   /* element offsets into the packed inputs/gradients */
+  int64_t oz, olam, onu;            /* element offsets into the packed outputs          */
+  int64_t ows;                      /* byte offset of the instance's workspace          */
+} qp_instance_desc;
+
+typedef struct qp_packed_sizes {
+  int64_t nQ, nq, nG, nh, nA, nb;   /* elements of each packed input (= its gradient)   */
+  int64_t nz, nlam, nnu;            /* elements of each packed output                   */
+  int64_t ws_bytes;                 /* workspace bytes, 256-byte aligned                */
+  int64_t fwd_smem, bwd_smem;       /* dynamic shared memory of the packed kernels      */
+  int32_t sw, ch;                   /* register-tile variant of the shared-memory path  */
+  int32_t n_global;                 /* instances on the global-memory path              */
+  int32_t reserved;
+} qp_packed_sizes;
+
+/* Host-side planning: dims is a HOST array of B triples (n, nineq, neq).  Fills the HOST
+ * arrays desc[B] (in execution order: largest estimated cost first) and *sizes.  The caller
+ * copies desc to device memory unchanged and passes it, with sizes, to the packed calls. */
+int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
+                   qp_instance_desc* desc, qp_packed_sizes* sizes);
+
+/* Forward pass of a packed batch (device pointers as in qp_forward, packed as above;
+ * status/iters/resid indexed by instance id; workspace of sizes->ws_bytes bytes). */
+int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
+                      const qp_packed_sizes* sizes, const void* Q, const void* q,
+                      const void* G, const void* h, const void* A, const void* b, void* z,
+                      void* lam, void* nu, int32_t* status, int32_t* iters, double* resid,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* Backward pass of a packed batch, after qp_forward_packed with the same desc, sizes and
+ * workspace.  dl_dz is packed like z; the gradients like the inputs. */
+int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
+                       const qp_packed_sizes* sizes, const void* Q, const void* G,
+                       const void* A, const void* workspace, size_t workspace_bytes,
+                       const void* dl_dz, void* dQ, void* dq, void* dG, void* dh, void* dA,
+                       void* db, void* stream);
+
 /* Human-readable text for a QP_E* code. */
 const char* qp_strerror(int code);
 

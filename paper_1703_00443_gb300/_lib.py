@@ -80,6 +80,18 @@ class QPOptions(ctypes.Structure):
                 ("path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class QPInstanceDesc(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("n", "nineq", "neq", "id", "nz", "flags")] + \
+               [(k, ctypes.c_int64) for k in ("oQ", "oq", "oG", "oh", "oA", "ob", "oz", "olam",
+                                              "onu", "ows")]
+
+
+class QPPackedSizes(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("nQ", "nq", "nG", "nh", "nA", "nb", "nz", "nlam",
+                                              "nnu", "ws_bytes", "fwd_smem", "bwd_smem")] + \
+               [(k, ctypes.c_int32) for k in ("sw", "ch", "n_global", "reserved")]
+
+
 EXPORTS = {
     "qp_default_options": (None, [c_int, ctypes.POINTER(QPOptions)]),
     "qp_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
@@ -91,6 +103,13 @@ EXPORTS = {
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                     + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 8),
     "qp_strerror": (ctypes.c_char_p, [c_int]),
+    "qp_packed_plan": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,
+                               ctypes.POINTER(QPInstanceDesc), ctypes.POINTER(QPPackedSizes)]),
+    "qp_forward_packed": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,
+                                  ctypes.POINTER(QPPackedSizes)] + [c_void_p] * 13 + [c_size_t, c_void_p]),
+    "qp_backward_packed": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,
+                                   ctypes.POINTER(QPPackedSizes)] + [c_void_p] * 4 + [c_size_t]
+                           + [c_void_p] * 8),
 }
 
 

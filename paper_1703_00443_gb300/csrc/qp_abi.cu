@@ -2,6 +2,9 @@
 // choice and launches.  No device memory is allocated here; the caller owns every buffer.
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "qp_gb300.h"
 #include "qp_launch.cuh"
 
@@ -107,6 +110,26 @@ Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
 }
 
 }  // namespace
+
+static_assert(sizeof(qp_instance_desc) == sizeof(qpk::PackedDesc), "descriptor layout");
+
+int num_sms() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  return v;
+}
+
+// Rough relative cost of one instance (FMA counts of the setup sweep, ~12 interior point
+// iterations and the backward solve; the global path runs about 3× slower per FMA); used
+// only to order the work queue largest first.
+double est_cost(int n, int nz, int p, int m, bool large) {
+  const double m1 = nz + m, N = m1 + p;
+  const double c = m1 * N * N + 12.0 * (p * (double)p * p / 3.0 + 2.0 * n * N) + N * N;
+  return large ? 3.0 * c : c;
+}
 
 namespace qpk {
 bool fwd_variant_exists(int esz, int SW, int CH) {
@@ -225,6 +248,136 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                              (double*)dG, (double*)dh, (double*)dA, (double*)db,
                              (const unsigned char*)workspace, pl.ws, o.refine};
     e = qpk::launch_bwd_f64(P, smem, st);
+  }
+  return e == cudaSuccess ? QP_OK : QP_ECUDA;
+}
+
+int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
+                   qp_instance_desc* desc, qp_packed_sizes* sizes) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || B < 0 || !sizes || (B > 0 && (!dims || !desc)))
+    return QP_EINVAL;
+  qp_options o;
+  if (opt) o = *opt; else qp_default_options(dtype, &o);
+  const int esz = dtype == QP_F32 ? 4 : 8;
+  qp_packed_sizes S{};
+  int64_t oQ = 0, oq = 0, oG = 0, oh = 0, oA = 0, ob = 0;
+  int64_t ows = 256;   // first 256 bytes: the two work-queue counters
+  int sw_need = 1, ch_need = 1;
+  size_t fsm = 0, bsm = 0;
+  std::vector<std::pair<double, int>> order;
+  for (int i = 0; i < B; ++i) {
+    const int n = dims[3 * i], p = dims[3 * i + 1], m = dims[3 * i + 2];
+    if (!dims_ok(1, n, p, m)) return QP_EINVAL;
+    const Plan pl = make_plan(dtype, n, p, m, o.path);
+    if (!pl.ok) return QP_EUNSUPPORTED;
+    qp_instance_desc& d = desc[i];
+    d.n = n; d.nineq = p; d.neq = m; d.id = i; d.nz = pl.nz; d.flags = pl.large ? 1 : 0;
+    d.oQ = oQ; d.oq = oq; d.oG = oG; d.oh = oh; d.oA = oA; d.ob = ob;
+    d.oz = oq; d.olam = oh; d.onu = ob; d.ows = ows;
+    oQ += (int64_t)n * n; oq += n; oG += (int64_t)p * n; oh += p; oA += (int64_t)m * n; ob += m;
+    ows += (int64_t)pl.ws;
+    if (!pl.large) {
+      sw_need = std::max(sw_need, pl.sw);
+      ch_need = std::max(ch_need, pl.ch);
+    } else {
+      ++S.n_global;
+    }
+    fsm = std::max(fsm, pl.fsmem);
+    bsm = std::max(bsm, pl.bsmem);
+    order.push_back({est_cost(n, pl.nz, p, m, pl.large), i});
+  }
+  // Register-tile variant covering every shared-memory-path instance.
+  int sw = 0, ch = 0;
+  const int sws[3] = {1, 2, 4};
+  for (int c = ch_need; c <= 2 && !sw; ++c)
+    for (int k = 0; k < 3; ++k)
+      if (sws[k] >= sw_need && qpk::fwd_variant_exists(esz, sws[k], c)) { sw = sws[k]; ch = c; break; }
+  if (!sw) return QP_EUNSUPPORTED;
+  // Execution order: largest estimated cost first (longest-processing-time schedule).
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+  std::vector<qp_instance_desc> tmp(desc, desc + B);
+  for (int k = 0; k < B; ++k) desc[k] = tmp[order[k].second];
+  S.nQ = oQ; S.nq = oq; S.nG = oG; S.nh = oh; S.nA = oA; S.nb = ob;
+  S.nz = oq; S.nlam = oh; S.nnu = ob;
+  S.ws_bytes = ows;
+  S.fwd_smem = (int64_t)fsm; S.bwd_smem = (int64_t)bsm;
+  S.sw = sw; S.ch = ch;
+  *sizes = S;
+  return QP_OK;
+}
+
+int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
+                      const qp_packed_sizes* sizes, const void* Q, const void* q,
+                      const void* G, const void* h, const void* A, const void* b, void* z,
+                      void* lam, void* nu, int32_t* status, int32_t* iters, double* resid,
+                      void* workspace, size_t workspace_bytes, void* stream) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || B < 0 || !sizes) return QP_EINVAL;
+  if (B == 0) return QP_OK;
+  if (!desc || !Q || !q || !z || !workspace) return QP_EINVAL;
+  if ((sizes->nG > 0 && (!G || !h)) || (sizes->nA > 0 && (!A || !b))) return QP_EINVAL;
+  if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
+  if ((int64_t)workspace_bytes < sizes->ws_bytes) return QP_ENOSPACE;
+  if ((size_t)sizes->fwd_smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
+  qp_options o;
+  if (opt) o = *opt; else qp_default_options(dtype, &o);
+  if (o.max_iter < 0) return QP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(workspace, 0, 8, st) != cudaSuccess) return QP_ECUDA;
+  const int grid = std::min(B, num_sms());
+  cudaError_t e;
+  if (dtype == QP_F32) {
+    qpk::PackedFwdParams<float> P{B, (const qpk::PackedDesc*)desc, (int*)workspace,
+                                  (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
+                                  (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
+                                  status, iters, resid, (unsigned char*)workspace,
+                                  o.tol, o.mu_tol, o.max_iter};
+    e = qpk::launch_fwd_packed_f32(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid, st);
+  } else {
+    qpk::PackedFwdParams<double> P{B, (const qpk::PackedDesc*)desc, (int*)workspace,
+                                   (const double*)Q, (const double*)q, (const double*)G,
+                                   (const double*)h, (const double*)A, (const double*)b,
+                                   (double*)z, (double*)lam, (double*)nu, status, iters, resid,
+                                   (unsigned char*)workspace, o.tol, o.mu_tol, o.max_iter};
+    e = qpk::launch_fwd_packed_f64(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid, st);
+  }
+  return e == cudaSuccess ? QP_OK : QP_ECUDA;
+}
+
+int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
+                       const qp_packed_sizes* sizes, const void* Q, const void* G,
+                       const void* A, const void* workspace, size_t workspace_bytes,
+                       const void* dl_dz, void* dQ, void* dq, void* dG, void* dh, void* dA,
+                       void* db, void* stream) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || B < 0 || !sizes) return QP_EINVAL;
+  if (B == 0) return QP_OK;
+  if (!desc || !Q || !dl_dz || !workspace) return QP_EINVAL;
+  if ((sizes->nG > 0 && !G) || (sizes->nA > 0 && !A)) return QP_EINVAL;
+  if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
+  if ((int64_t)workspace_bytes < sizes->ws_bytes) return QP_ENOSPACE;
+  if ((size_t)sizes->bwd_smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
+  qp_options o;
+  if (opt) o = *opt; else qp_default_options(dtype, &o);
+  if (o.refine < 0 || o.refine > 4) return QP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // The backward counter is the second int of the workspace (the forward leaves it alone).
+  if (cudaMemsetAsync((char*)workspace + 4, 0, 4, st) != cudaSuccess) return QP_ECUDA;
+  const int grid = std::min(B, num_sms());
+  int* ctr = (int*)((char*)const_cast<void*>(workspace) + 4);
+  cudaError_t e;
+  if (dtype == QP_F32) {
+    qpk::PackedBwdParams<float> P{B, (const qpk::PackedDesc*)desc, ctr, (const float*)Q,
+                                  (const float*)G, (const float*)A, (const float*)dl_dz,
+                                  (float*)dQ, (float*)dq, (float*)dG, (float*)dh, (float*)dA,
+                                  (float*)db, (const unsigned char*)workspace, o.refine};
+    e = qpk::launch_bwd_packed_f32(P, (size_t)sizes->bwd_smem, grid, st);
+  } else {
+    qpk::PackedBwdParams<double> P{B, (const qpk::PackedDesc*)desc, ctr, (const double*)Q,
+                                   (const double*)G, (const double*)A, (const double*)dl_dz,
+                                   (double*)dQ, (double*)dq, (double*)dG, (double*)dh,
+                                   (double*)dA, (double*)db, (const unsigned char*)workspace,
+                                   o.refine};
+    e = qpk::launch_bwd_packed_f64(P, (size_t)sizes->bwd_smem, grid, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;
 }

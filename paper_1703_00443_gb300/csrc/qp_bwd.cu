@@ -19,4 +19,20 @@ cudaError_t launch_bwd_f64(const BwdParams<double>& P, size_t smem, cudaStream_t
   return cudaGetLastError();
 }
 
+cudaError_t launch_bwd_packed_f32(const PackedBwdParams<float>& P, size_t smem, int grid, cudaStream_t st) {
+  auto k = qp_bwd_packed_kernel<float>;
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NTHREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_packed_f64(const PackedBwdParams<double>& P, size_t smem, int grid, cudaStream_t st) {
+  auto k = qp_bwd_packed_kernel<double>;
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NTHREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
 }  // namespace qpk

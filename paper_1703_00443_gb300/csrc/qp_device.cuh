@@ -147,6 +147,61 @@ struct FwdParams {
   int max_iter;
 };
 
+// Per-instance views used by the kernel bodies (built from the fixed-size parameters or from
+// a packed-batch descriptor).
+template <typename T>
+struct FwdInst {
+  int n, p, m, nz;
+  const T *Q, *q, *G, *h, *A, *b;
+  T *z, *lam, *nu;
+  int32_t *status, *iters;   // this instance's slots (or null)
+  double* resid;             // this instance's four residual values (or null)
+  unsigned char* ws;         // this instance's workspace
+  double tol, mu_tol;
+  int max_iter;
+};
+
+template <typename T>
+struct BwdInst {
+  int n, p, m, nz, large;
+  const T *Q, *G, *A, *dl_dz;
+  T *dQ, *dq, *dG, *dh, *dA, *db;
+  const unsigned char* ws;
+  int refine;
+};
+
+// Descriptor of one instance of a packed (uneven) batch; the C ABI's qp_instance_desc has
+// the same layout.
+struct PackedDesc {
+  int32_t n, nineq, neq, id, nz, flags;
+  int64_t oQ, oq, oG, oh, oA, ob, oz, olam, onu, ows;
+};
+
+template <typename T>
+struct PackedFwdParams {
+  int B;
+  const PackedDesc* desc;
+  int* counter;
+  const T *Q, *q, *G, *h, *A, *b;
+  T *z, *lam, *nu;
+  int32_t *status, *iters;
+  double* resid;
+  unsigned char* ws;
+  double tol, mu_tol;
+  int max_iter;
+};
+
+template <typename T>
+struct PackedBwdParams {
+  int B;
+  const PackedDesc* desc;
+  int* counter;
+  const T *Q, *G, *A, *dl_dz;
+  T *dQ, *dq, *dG, *dh, *dA, *db;
+  const unsigned char* ws;
+  int refine;
+};
+
 template <typename T>
 struct BwdParams {
   int B, n, p, m, nz;
@@ -1037,11 +1092,11 @@ namespace qpk {
 // M + D(dsh) into X.  With ws_resident the factors already live in the workspace, otherwise
 // they are copied there for the backward pass.
 template <typename T, typename FS, typename FF>
-__device__ __forceinline__ void fwd_body(const FwdParams<T>& P, const FwdSmem<T>& L,
+__device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& L,
                                          unsigned char* sm, T* SR, T* Mb, T* dM,
                                          bool ws_resident, FS setup, FF factor) {
   using V = typename Split<T>::V;
-  const int bi = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int n = P.n, p = P.p, m = P.m;
   const int m1 = L.m1, nz = L.nz;
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
@@ -1060,15 +1115,15 @@ __device__ __forceinline__ void fwd_body(const FwdParams<T>& P, const FwdSmem<T>
   const int kscr = (int)(L.cbytes / sizeof(Acc<T>));
   (void)cb;
 
-  const T* Qb = P.Q + (size_t)bi * n * n;
-  const T* qb = P.q + (size_t)bi * n;
-  const T* Gb = p ? P.G + (size_t)bi * p * n : nullptr;
-  const T* hb = p ? P.h + (size_t)bi * p : nullptr;
-  const T* Ab = m ? P.A + (size_t)bi * m * n : nullptr;
-  const T* bb = m ? P.b + (size_t)bi * m : nullptr;
+  const T* Qb = P.Q;
+  const T* qb = P.q;
+  const T* Gb = p ? P.G : nullptr;
+  const T* hb = p ? P.h : nullptr;
+  const T* Ab = m ? P.A : nullptr;
+  const T* bb = m ? P.b : nullptr;
   WsLayout W;
   W.init(n, nz, p, m, (int)sizeof(T), ws_resident);
-  unsigned char* wsb = P.ws + (size_t)bi * P.ws_inst;
+  unsigned char* wsb = P.ws;
   T* wSR = reinterpret_cast<T*>(wsb + W.oSR);
   T* wX = reinterpret_cast<T*>(wsb + W.oX);
   double* wIt = reinterpret_cast<double*>(wsb + W.oIt);
@@ -1278,83 +1333,150 @@ __device__ __forceinline__ void fwd_body(const FwdParams<T>& P, const FwdSmem<T>
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   for (int i = tid; i < n; i += NTHREADS) {
     const double v = bad ? qnan : z[i];
-    P.z[(size_t)bi * n + i] = (T)v;
+    P.z[i] = (T)v;
     wIt[i] = v;
   }
   for (int i = tid; i < p; i += NTHREADS) {
     const double vs = bad ? qnan : s[i], vl = bad ? qnan : lam[i];
-    if (P.lam) P.lam[(size_t)bi * p + i] = (T)vl;
+    if (P.lam) P.lam[i] = (T)vl;
     wIt[n + i] = vs;
     wIt[n + p + i] = vl;
   }
   for (int i = tid; i < m; i += NTHREADS) {
     const double v = bad ? qnan : nu[i];
-    if (P.nu) P.nu[(size_t)bi * m + i] = (T)v;
+    if (P.nu) P.nu[i] = (T)v;
     wIt[n + 2 * p + i] = v;
   }
   if (!bad && !ws_resident)
     for (int i = tid; i < p * p; i += NTHREADS) wX[i] = Mb[i];
   if (tid == 0) {
     wSt[0] = status;
-    if (P.status) P.status[bi] = status;
-    if (P.iters) P.iters[bi] = it;
+    if (P.status) *P.status = status;
+    if (P.iters) *P.iters = it;
     if (P.resid) {
-      P.resid[4 * (size_t)bi + 0] = last[0];
-      P.resid[4 * (size_t)bi + 1] = last[1];
-      P.resid[4 * (size_t)bi + 2] = last[2];
-      P.resid[4 * (size_t)bi + 3] = last[3];
+      P.resid[0] = last[0];
+      P.resid[1] = last[1];
+      P.resid[2] = last[2];
+      P.resid[3] = last[3];
     }
   }
 }
 
 
-// Shared-memory kernel: S/RE and M/X held in shared memory, register-tile factorisations.
+template <typename T>
+__device__ __forceinline__ FwdInst<T> fixed_inst(const FwdParams<T>& P, int bi) {
+  const int n = P.n, p = P.p, m = P.m;
+  FwdInst<T> I;
+  I.n = n; I.p = p; I.m = m; I.nz = P.nz;
+  I.Q = P.Q + (size_t)bi * n * n;
+  I.q = P.q + (size_t)bi * n;
+  I.G = p ? P.G + (size_t)bi * p * n : nullptr;
+  I.h = p ? P.h + (size_t)bi * p : nullptr;
+  I.A = m ? P.A + (size_t)bi * m * n : nullptr;
+  I.b = m ? P.b + (size_t)bi * m : nullptr;
+  I.z = P.z + (size_t)bi * n;
+  I.lam = P.lam ? P.lam + (size_t)bi * p : nullptr;
+  I.nu = P.nu ? P.nu + (size_t)bi * m : nullptr;
+  I.status = P.status ? P.status + bi : nullptr;
+  I.iters = P.iters ? P.iters + bi : nullptr;
+  I.resid = P.resid ? P.resid + 4 * (size_t)bi : nullptr;
+  I.ws = P.ws + (size_t)bi * P.ws_inst;
+  I.tol = P.tol; I.mu_tol = P.mu_tol; I.max_iter = P.max_iter;
+  return I;
+}
+
+// One instance on the shared-memory path (factors in shared memory, register tiles).
 template <typename T, int SW, int CH>
-__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> P) {
-  extern __shared__ __align__(16) unsigned char sm[];
+__device__ __forceinline__ void fwd_smem_path(const FwdInst<T>& I, unsigned char* sm) {
   FwdSmem<T> L;
-  L.init(P.n, P.nz, P.p, P.m, false);
+  L.init(I.n, I.nz, I.p, I.m, false);
   T* SR = reinterpret_cast<T*>(sm + L.oSR);
   T* Mb = reinterpret_cast<T*>(sm + L.oMb);
   T* dM = reinterpret_cast<T*>(sm + L.odM);
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
-  const int n = P.n, p = P.p, m = P.m;
-  fwd_body<T>(P, L, sm, SR, Mb, dM, false,
+  const int n = I.n, p = I.p, m = I.m;
+  fwd_body<T>(I, L, sm, SR, Mb, dM, false,
       [&](const T* Qb, const T* Ab, const T* Gb) {
         return sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
       },
       [&](const T* dsh) { return chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb); });
 }
 
-// Global-memory kernel: the factors live in the instance's workspace (see qp_large.cuh).
+// One instance on the global-memory path (factors in the workspace, see qp_large.cuh).
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_large_kernel(const FwdParams<T> P) {
-  extern __shared__ __align__(16) unsigned char sm[];
+__device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned char* sm) {
   FwdSmem<T> L;
-  L.init(P.n, P.nz, P.p, P.m, true);
-  const int n = P.n, p = P.p, m = P.m, nz = P.nz;
+  L.init(I.n, I.nz, I.p, I.m, true);
+  const int n = I.n, p = I.p, m = I.m, nz = I.nz;
   WsLayout W;
   W.init(n, nz, p, m, (int)sizeof(T), true);
-  unsigned char* wsb = P.ws + (size_t)blockIdx.x * P.ws_inst;
-  T* SR = reinterpret_cast<T*>(wsb + W.oSR);
-  T* Mb = reinterpret_cast<T*>(wsb + W.oX);
-  T* dM = reinterpret_cast<T*>(wsb + W.odM);
-  T* Aw = reinterpret_cast<T*>(wsb + W.oAw);
-  T* pan = reinterpret_cast<T*>(wsb + W.oPan);
+  T* SR = reinterpret_cast<T*>(I.ws + W.oSR);
+  T* Mb = reinterpret_cast<T*>(I.ws + W.oX);
+  T* dM = reinterpret_cast<T*>(I.ws + W.odM);
+  T* Aw = reinterpret_cast<T*>(I.ws + W.oAw);
+  T* pan = reinterpret_cast<T*>(I.ws + W.oPan);
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
-  fwd_body<T>(P, L, sm, SR, Mb, dM, true,
+  fwd_body<T>(I, L, sm, SR, Mb, dM, true,
       [&](const T* Qb, const T* Ab, const T* Gb) {
         return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, cb);
       },
       [&](const T* dsh) { return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, cb); });
 }
 
+// Fixed-size batch, shared-memory path: one block per instance.
+template <typename T, int SW, int CH>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  fwd_smem_path<T, SW, CH>(fixed_inst(P, blockIdx.x), sm);
+}
+
+// Fixed-size batch, global-memory path.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_large_kernel(const FwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  fwd_global_path<T>(fixed_inst(P, blockIdx.x), sm);
+}
+
+// Packed batch of uneven sizes in one persistent launch: blocks take instances from an atomic
+// counter in the order of the descriptor array (largest estimated cost first), and each
+// instance runs the path its own size selects, so its result does not depend on the mix.
+template <typename T, int SW, int CH>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const PackedFwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int k = s_idx;
+    __syncthreads();
+    if (k >= P.B) break;
+    const PackedDesc d = P.desc[k];
+    FwdInst<T> I;
+    I.n = d.n; I.p = d.nineq; I.m = d.neq; I.nz = d.nz;
+    I.Q = P.Q + d.oQ; I.q = P.q + d.oq;
+    I.G = d.nineq ? P.G + d.oG : nullptr;
+    I.h = d.nineq ? P.h + d.oh : nullptr;
+    I.A = d.neq ? P.A + d.oA : nullptr;
+    I.b = d.neq ? P.b + d.ob : nullptr;
+    I.z = P.z + d.oz;
+    I.lam = P.lam ? P.lam + d.olam : nullptr;
+    I.nu = P.nu ? P.nu + d.onu : nullptr;
+    I.status = P.status ? P.status + d.id : nullptr;
+    I.iters = P.iters ? P.iters + d.id : nullptr;
+    I.resid = P.resid ? P.resid + 4 * (size_t)d.id : nullptr;
+    I.ws = P.ws + d.ows;
+    I.tol = P.tol; I.mu_tol = P.mu_tol; I.max_iter = P.max_iter;
+    if (d.flags & 1) fwd_global_path<T>(I, sm);
+    else fwd_smem_path<T, SW, CH>(I, sm);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ backward kernel
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> P) {
+__device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm) {
   using V = typename Split<T>::V;
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int bi = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int n = P.n, p = P.p, m = P.m, nz = P.nz, m1 = nz + m;
   BwdSmem<T> L;
   L.init(n, nz, p, m);
@@ -1371,24 +1493,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
 
   WsLayout W;
   W.init(n, nz, p, m, (int)sizeof(T), P.large != 0);
-  const unsigned char* wsb = P.ws + (size_t)bi * P.ws_inst;
+  const unsigned char* wsb = P.ws;
   const T* SR = reinterpret_cast<const T*>(wsb + W.oSR);
   const T* X = reinterpret_cast<const T*>(wsb + W.oX);
   const double* wIt = reinterpret_cast<const double*>(wsb + W.oIt);
   const int status = reinterpret_cast<const int32_t*>(wsb + W.oSt)[0];
-  const T* Qb = P.Q + (size_t)bi * n * n;
-  const T* Gb = p ? P.G + (size_t)bi * p * n : nullptr;
-  const T* Ab = m ? P.A + (size_t)bi * m * n : nullptr;
-  const T* gz = P.dl_dz + (size_t)bi * n;
+  const T* Qb = P.Q;
+  const T* Gb = p ? P.G : nullptr;
+  const T* Ab = m ? P.A : nullptr;
+  const T* gz = P.dl_dz;
 
   if (status == ST_NOTPD || status == ST_NUM) {
     const T qn = (T)__longlong_as_double(0x7ff8000000000000LL);
-    if (P.dQ) for (int i = tid; i < n * n; i += NTHREADS) P.dQ[(size_t)bi * n * n + i] = qn;
-    if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[(size_t)bi * n + i] = qn;
-    if (P.dG) for (int i = tid; i < p * n; i += NTHREADS) P.dG[(size_t)bi * p * n + i] = qn;
-    if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[(size_t)bi * p + i] = qn;
-    if (P.dA) for (int i = tid; i < m * n; i += NTHREADS) P.dA[(size_t)bi * m * n + i] = qn;
-    if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[(size_t)bi * m + i] = qn;
+    if (P.dQ) for (int i = tid; i < n * n; i += NTHREADS) P.dQ[i] = qn;
+    if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[i] = qn;
+    if (P.dG) for (int i = tid; i < p * n; i += NTHREADS) P.dG[i] = qn;
+    if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[i] = qn;
+    if (P.dA) for (int i = tid; i < m * n; i += NTHREADS) P.dA[i] = qn;
+    if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[i] = qn;
     return;
   }
   for (int i = tid; i < n + 2 * p + m; i += NTHREADS) dv[i] = wIt[i];
@@ -1468,29 +1590,82 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   for (int i = tid; i < m; i += NTHREADS) { vnu[i] = (T)nu[i]; vdnu[i] = (T)dnu[i]; }
   __syncthreads();
   if (P.dQ) {
-    T* o = P.dQ + (size_t)bi * n * n;
+    T* o = P.dQ;
     for (int e = tid; e < n * n; e += NTHREADS) {
       const int i = e / n, j = e - i * n;
       o[e] = T(0.5) * fma(vdz[i], vz[j], vz[i] * vdz[j]);
     }
   }
-  if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[(size_t)bi * n + i] = vdz[i];
+  if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[i] = vdz[i];
   if (P.dG) {
-    T* o = P.dG + (size_t)bi * p * n;
+    T* o = P.dG;
     for (int e = tid; e < p * n; e += NTHREADS) {
       const int i = e / n, j = e - i * n;
       o[e] = fma(vdl[i], vz[j], vl[i] * vdz[j]);
     }
   }
-  if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[(size_t)bi * p + i] = -vdl[i];
+  if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[i] = -vdl[i];
   if (P.dA) {
-    T* o = P.dA + (size_t)bi * m * n;
+    T* o = P.dA;
     for (int e = tid; e < m * n; e += NTHREADS) {
       const int i = e / n, j = e - i * n;
       o[e] = fma(vdnu[i], vz[j], vnu[i] * vdz[j]);
     }
   }
-  if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[(size_t)bi * m + i] = -vdnu[i];
+  if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[i] = -vdnu[i];
+}
+
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int bi = blockIdx.x, n = P.n, p = P.p, m = P.m;
+  BwdInst<T> I;
+  I.n = n; I.p = p; I.m = m; I.nz = P.nz; I.large = P.large;
+  I.Q = P.Q + (size_t)bi * n * n;
+  I.G = p ? P.G + (size_t)bi * p * n : nullptr;
+  I.A = m ? P.A + (size_t)bi * m * n : nullptr;
+  I.dl_dz = P.dl_dz + (size_t)bi * n;
+  I.dQ = P.dQ ? P.dQ + (size_t)bi * n * n : nullptr;
+  I.dq = P.dq ? P.dq + (size_t)bi * n : nullptr;
+  I.dG = P.dG ? P.dG + (size_t)bi * p * n : nullptr;
+  I.dh = P.dh ? P.dh + (size_t)bi * p : nullptr;
+  I.dA = P.dA ? P.dA + (size_t)bi * m * n : nullptr;
+  I.db = P.db ? P.db + (size_t)bi * m : nullptr;
+  I.ws = P.ws + (size_t)bi * P.ws_inst;
+  I.refine = P.refine;
+  bwd_body<T>(I, sm);
+}
+
+// Backward pass of a packed batch, persistent like its forward kernel.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_packed_kernel(const PackedBwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int k = s_idx;
+    __syncthreads();
+    if (k >= P.B) break;
+    const PackedDesc d = P.desc[k];
+    BwdInst<T> I;
+    I.n = d.n; I.p = d.nineq; I.m = d.neq; I.nz = d.nz; I.large = d.flags & 1;
+    I.Q = P.Q + d.oQ;
+    I.G = d.nineq ? P.G + d.oG : nullptr;
+    I.A = d.neq ? P.A + d.oA : nullptr;
+    I.dl_dz = P.dl_dz + d.oq;
+    I.dQ = P.dQ ? P.dQ + d.oQ : nullptr;
+    I.dq = P.dq ? P.dq + d.oq : nullptr;
+    I.dG = P.dG ? P.dG + d.oG : nullptr;
+    I.dh = P.dh ? P.dh + d.oh : nullptr;
+    I.dA = P.dA ? P.dA + d.oA : nullptr;
+    I.db = P.db ? P.db + d.ob : nullptr;
+    I.ws = P.ws + d.ows;
+    I.refine = P.refine;
+    bwd_body<T>(I, sm);
+    __syncthreads();
+  }
 }
 
 }  // namespace qpk

@@ -26,4 +26,20 @@ cudaError_t launch_fwd_large_f64(const FwdParams<double>& P, size_t smem, cudaSt
   return cudaGetLastError();
 }
 
+template <int SW, int CH>
+static cudaError_t gop(const PackedFwdParams<double>& P, size_t smem, int grid, cudaStream_t st) {
+  auto k = qp_fwd_packed_kernel<double, SW, CH>;
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NTHREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_packed_f64(const PackedFwdParams<double>& P, int SW, int CH, size_t smem,
+                                  int grid, cudaStream_t st) {
+  if (SW == 1 && CH == 1) return gop<1, 1>(P, smem, grid, st);
+  if (SW == 2 && CH == 1) return gop<2, 1>(P, smem, grid, st);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace qpk

@@ -1,0 +1,108 @@
+"""Packed (uneven) batches: one persistent launch per direction, each instance on the path
+its own size selects; results must equal the same instance solved alone and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward
+from paper_1703_00443_gb300.packed import PackedBatch
+from tests.helpers import grad_floor, oracle_solve_and_grad, rel_err
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+NAMES = ("dQ", "dq", "dG", "dh", "dA", "db")
+
+
+def _instances(sizes, seed=0):
+    return [inputs.random_qp(n, p, m, workload=inputs.WL_UNEVEN, index=i, seed=seed)
+            for i, (n, p, m) in enumerate(sizes)]
+
+
+def _grads_in(sizes, seed=0):
+    return [inputs.upstream_grad(1, n, workload=inputs.WL_UNEVEN, start=i, seed=seed)[0]
+            for i, (n, p, m) in enumerate(sizes)]
+
+
+def _solve_packed(sizes, inst, gin):
+    pb = PackedBatch(sizes, device=DEV)
+    Qp, qp, Gp, hp, Ap, bp = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
+    out = pb.forward(Qp, qp, Gp, hp, Ap, bp)
+    grads = pb.backward(Qp, Gp, Ap, pb.pack_vec([np.float32(g) for g in gin], "q"))
+    torch.cuda.synchronize()
+    res = dict(z=pb.unpack(out.z, "q"), lam=pb.unpack(out.lam, "h"), nu=pb.unpack(out.nu, "b"),
+               status=out.status[: len(sizes)].cpu().numpy())
+    for k, key, gbuf in zip(NAMES, pb.KEYS, grads):
+        res[k] = pb.unpack(gbuf, key)
+    return pb, res
+
+
+def test_packed_equals_each_instance_alone():
+    sizes = [(12, 9, 2), (100, 100, 50), (7, 13, 3), (140, 200, 30), (33, 40, 8), (64, 64, 16),
+             (150, 90, 37)]
+    inst = _instances(sizes, seed=5)
+    gin = _grads_in(sizes, seed=5)
+    pb, res = _solve_packed(sizes, inst, gin)
+    assert pb.n_global >= 1 and pb.n_global < len(sizes)   # both kernel paths in one launch
+    assert (res["status"] == 0).all()
+    for i, t in enumerate(inst):
+        T = [torch.from_numpy(np.float32(x)).unsqueeze(0).to(DEV) for x in t]
+        f = qp_forward(*T)
+        g = qp_backward(f, torch.from_numpy(np.float32(gin[i])).unsqueeze(0).to(DEV))
+        torch.cuda.synchronize()
+        assert torch.equal(f.z[0], res["z"][i]), i
+        assert torch.equal(f.lam[0], res["lam"][i]), i
+        for k, gg in zip(NAMES, g):
+            assert torch.equal(gg[0], res[k][i]), (i, k)
+
+
+def test_packed_uneven_sample_matches_oracle():
+    sizes = inputs.uneven_sizes(24)
+    inst = _instances(sizes)
+    gin = _grads_in(sizes)
+    pb, res = _solve_packed(sizes, inst, gin)
+    assert (res["status"] == 0).all(), res["status"]
+    for i, (t, g) in enumerate(zip(inst, gin)):
+        import oracle
+        Q, q, G, h, A, b = (np.asarray(x, dtype=np.float64) for x in t)
+        sol = oracle.solve(Q, q, G, h, A, b)
+        gr = oracle.backward(Q, G, h, A, sol, np.float64(np.float32(g)))
+        ez = rel_err(res["z"][i].double().cpu().numpy()[None], sol["z"][None])[0]
+        assert ez <= 1e-5, (i, sizes[i], ez)
+        for k in NAMES:
+            ref = gr[k]
+            if ref.size == 0:
+                continue
+            fl = grad_floor(k, np.float32(g)[None], sol["z"][None])
+            e = rel_err(res[k][i].double().cpu().numpy()[None], ref[None], fl)[0]
+            assert e <= 1e-4, (i, sizes[i], k, e)
+
+
+def test_packed_cuda_graph_replay_matches_eager():
+    sizes = [(20, 30, 5), (90, 100, 20), (150, 120, 30), (40, 10, 0)]
+    inst = _instances(sizes, seed=11)
+    gin = _grads_in(sizes, seed=11)
+    pb = PackedBatch(sizes, device=DEV)
+    Qp, qp, Gp, hp, Ap, bp = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
+    gl = pb.pack_vec([np.float32(g) for g in gin], "q")
+    eager = pb.forward(Qp, qp, Gp, hp, Ap, bp)
+    eg = pb.backward(Qp, Gp, Ap, gl)
+    torch.cuda.synchronize()
+    ez, egrads = eager.z.clone(), [t.clone() for t in eg]
+    # capture forward + backward with static buffers, then replay on the same data
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fout = pb.forward(Qp, qp, Gp, hp, Ap, bp)
+        gout = pb.backward(Qp, Gp, Ap, gl)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fout = pb.forward(Qp, qp, Gp, hp, Ap, bp, out=fout)
+        gout = pb.backward(Qp, Gp, Ap, gl, out=gout)
+    for _ in range(2):
+        fout.z.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(fout.z, ez)
+        for a, b in zip(gout, egrads):
+            assert torch.equal(a, b)
