@@ -26,7 +26,7 @@ int max_smem_optin() {
 }
 
 bool dims_ok(int B, int n, int nineq, int neq) {
-  return B >= 0 && n >= 1 && nineq >= 0 && neq >= 0 && neq <= n;
+  return B >= 0 && n >= 1 && n <= 2048 && nineq >= 0 && neq >= 0 && neq <= n;
 }
 
 int tiles_of(int N) {
@@ -274,7 +274,10 @@ int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
     d.n = n; d.nineq = p; d.neq = m; d.id = i; d.nz = pl.nz; d.flags = pl.large ? 1 : 0;
     d.oQ = oQ; d.oq = oq; d.oG = oG; d.oh = oh; d.oA = oA; d.ob = ob;
     d.oz = oq; d.olam = oh; d.onu = ob; d.ows = ows;
-    oQ += (int64_t)n * n; oq += n; oG += (int64_t)p * n; oh += p; oA += (int64_t)m * n; ob += m;
+    // Offsets padded to multiples of 4 elements keep every instance's rows 16-byte aligned.
+    auto r4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
+    oQ += r4((int64_t)n * n); oq += r4(n); oG += r4((int64_t)p * n); oh += r4(p);
+    oA += r4((int64_t)m * n); ob += r4(m);
     ows += (int64_t)pl.ws;
     if (!pl.large) {
       sw_need = std::max(sw_need, pl.sw);

@@ -436,14 +436,29 @@ __device__ __forceinline__ void ldg4(double (&v)[4], const double* p) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// Four consecutive elements of a row, columns c0..c0+3 clipped to n: one 16-byte load when
+// the address allows it, scalar loads otherwise.  The values (and so every result below) do
+// not depend on which form is taken.
+template <typename T>
+__device__ __forceinline__ void ldg4_row(T (&v)[4], const T* row, int c0, int n, bool vec) {
+  if (vec && c0 + 4 <= n) {
+    ldg4(v, row + c0);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = (c0 + c < n) ? __ldg(row + c0 + c) : T(0);
+  }
+}
+
 // FP64-accurate application of the (unreduced, slack-eliminated) KKT operator:
 //   out_z = Q x_z + Gᵀ x_λ + Aᵀ x_ν + add_z,  out_λ = G x_z + add_λ,  out_ν = A x_z + add_ν.
 // x = [x_z; x_λ; x_ν] is given split (FP32 hi/lo pairs for T = float).  Q is symmetric, so
 // Q x_z is formed column-wise together with Gᵀx_λ and Aᵀx_ν from one pass over the rows of
 // [Q; G; A] (inputs read from global memory, where they stay L2-resident); G x_z and A x_z
-// come from a row pass.  When n is a multiple of 4 every thread reads four consecutive
-// columns per 16-byte load.  Partial sums stay double-float until one conversion per output
-// element.  `scr` holds kscr ≥ NTHREADS accumulators.  Ends with a barrier.
+// come from a row pass.  Work is split into quads of four columns; each thread reads a quad
+// with one 16-byte load when n is a multiple of 4 and the rows are aligned, else with
+// scalar loads, in the same order either way.  Partial sums stay double-float until one
+// conversion per output element.  `scr` holds kscr ≥ NTHREADS accumulators.  Ends with a
+// barrier.
 template <typename T, typename FZ, typename FL, typename FN>
 __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restrict__ Q,
                                           const T* __restrict__ G, const T* __restrict__ A,
@@ -456,82 +471,40 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restri
   auto rowp = [&](int r) -> const T* {
     return r < n ? Q + (size_t)r * n : (r < n + p ? G + (size_t)(r - n) * n : A + (size_t)(r - n - p) * n);
   };
-  const bool vec4 = (n % 4 == 0) &&
+  const bool vec = (n % 4 == 0) &&
       ((((uintptr_t)Q) | ((uintptr_t)G) | ((uintptr_t)A)) % (4 * sizeof(T)) == 0);
-  int nparts = 0;   // > 0: column partials in scr[part·n + j] to be merged below
-  if (vec4) {
-    const int nq = n / 4;
-    nparts = min(NTHREADS / nq, kscr / n);
-    if (nparts >= 1) {
-      const int jq = tid % nq, part = tid / nq;
-      if (part < nparts) {
-        const int chunk = (R + nparts - 1) / nparts;
-        const int r0 = part * chunk, r1 = min(R, r0 + chunk);
-        Acc<T> acc[4];
-        int r = r0;
-        for (; r + 4 <= r1; r += 4) {
-          T av[4][4];
+  const int nq = (n + 3) / 4;
+  const int nparts = max(1, min(NTHREADS / nq, kscr / (4 * nq)));
+  // Column pass: thread (jq, part) sums rows [r0, r1) of columns 4jq .. 4jq+3.
+  for (int t = tid; t < nq * nparts; t += NTHREADS) {
+    const int jq = t % nq, part = t / nq;
+    const int chunk = (R + nparts - 1) / nparts;
+    const int r0 = part * chunk, r1 = min(R, r0 + chunk);
+    Acc<T> acc[4];
+    int r = r0;
+    for (; r + 4 <= r1; r += 4) {
+      T av[4][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) ldg4(av[u], rowp(r + u) + 4 * jq);
+      for (int u = 0; u < 4; ++u) ldg4_row(av[u], rowp(r + u), 4 * jq, n, vec);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const V x = xv[r + u];
+      for (int u = 0; u < 4; ++u) {
+        const V x = xv[r + u];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c].add(av[u][c], x);
-          }
-        }
-        for (; r < r1; ++r) {
-          T av[4];
-          ldg4(av, rowp(r) + 4 * jq);
-          const V x = xv[r];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[c].add(av[c], x);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) scr[part * n + 4 * jq + c] = acc[c];
-      }
-    } else {
-      nparts = 0;
-      for (int jq = tid; jq < nq; jq += NTHREADS) {
-        Acc<T> acc[4];
-        for (int r = 0; r < R; ++r) {
-          T av[4];
-          ldg4(av, rowp(r) + 4 * jq);
-          const V x = xv[r];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[c].add(av[c], x);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) out_z[4 * jq + c] = acc[c].value() + add_z(4 * jq + c);
+        for (int c = 0; c < 4; ++c) acc[c].add(av[u][c], x);
       }
     }
-  } else if (n <= NTHREADS / 2) {
-    nparts = min(NTHREADS, kscr) / n;
-    const int j = tid % n, part = tid / n;
-    if (part < nparts) {
-      const int chunk = (R + nparts - 1) / nparts;
-      const int r0 = part * chunk, r1 = min(R, r0 + chunk);
-      Acc<T> acc;
-      int r = r0;
-      for (; r + 8 <= r1; r += 8) {
-        T av[8];
+    for (; r < r1; ++r) {
+      T av[4];
+      ldg4_row(av, rowp(r), 4 * jq, n, vec);
+      const V x = xv[r];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) av[u] = __ldg(rowp(r + u) + j);
+      for (int c = 0; c < 4; ++c) acc[c].add(av[c], x);
+    }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc.add(av[u], xv[r + u]);
-      }
-      for (; r < r1; ++r) acc.add(__ldg(rowp(r) + j), xv[r]);
-      scr[part * n + j] = acc;
-    }
-  } else {
-    for (int j = tid; j < n; j += NTHREADS) {
-      Acc<T> acc;
-      for (int r = 0; r < R; ++r) acc.add(__ldg(rowp(r) + j), xv[r]);
-      out_z[j] = acc.value() + add_z(j);
-    }
+    for (int c = 0; c < 4; ++c) scr[part * 4 * nq + 4 * jq + c] = acc[c];
   }
-  // Row pass: G x_z and A x_z with GL lanes per row, two rows per lane group at a time so
-  // that both rows' loads are in flight together.
+  // Row pass: G x_z and A x_z with GL lanes per row (lane gl takes quads gl, gl+GL, ...),
+  // two rows per lane group at a time so that both rows' loads are in flight together.
   {
     constexpr int GL = 8, NG = NTHREADS / GL, QB = 4;
     const int g = tid / GL, gl = tid % GL;
@@ -544,51 +517,31 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restri
         rowv[h2] = (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
       }
       Acc<T> acc[2];
-      if (vec4) {
-        const int nq = n / 4;
-        for (int qb0 = 0; qb0 < nq; qb0 += GL * QB) {
-          T av[2][QB][4];
+      for (int qb0 = 0; qb0 < nq; qb0 += GL * QB) {
+        T av[2][QB][4];
 #pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2)
+        for (int h2 = 0; h2 < 2; ++h2)
 #pragma unroll
-            for (int u = 0; u < QB; ++u) {
-              const int q = qb0 + gl + u * GL;
-              if (rr[h2] < p + m && q < nq) {
-                ldg4(av[h2][u], rowv[h2] + 4 * q);
-              } else {
+          for (int u = 0; u < QB; ++u) {
+            const int q = qb0 + gl + u * GL;
+            if (rr[h2] < p + m && q < nq) {
+              ldg4_row(av[h2][u], rowv[h2], 4 * q, n, vec);
+            } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) av[h2][u][c] = T(0);
-              }
+              for (int c = 0; c < 4; ++c) av[h2][u][c] = T(0);
             }
+          }
 #pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2)
+        for (int h2 = 0; h2 < 2; ++h2)
 #pragma unroll
-            for (int u = 0; u < QB; ++u) {
-              const int q = qb0 + gl + u * GL;
-              if (rr[h2] < p + m && q < nq) {
+          for (int u = 0; u < QB; ++u) {
+            const int q = qb0 + gl + u * GL;
+            if (rr[h2] < p + m && q < nq) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[h2].add(av[h2][u][c], xv[4 * q + c]);
-              }
+              for (int c = 0; c < 4; ++c)
+                if (4 * q + c < n) acc[h2].add(av[h2][u][c], xv[4 * q + c]);
             }
-        }
-      } else {
-        for (int cb0 = 0; cb0 < n; cb0 += GL * 8) {
-          T av[2][8];
-#pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int c = cb0 + gl + u * GL;
-              av[h2][u] = (rr[h2] < p + m && c < n) ? __ldg(rowv[h2] + c) : T(0);
-            }
-#pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int c = cb0 + gl + u * GL;
-              if (rr[h2] < p + m && c < n) acc[h2].add(av[h2][u], xv[c]);
-            }
-        }
+          }
       }
 #pragma unroll
       for (int h2 = 0; h2 < 2; ++h2) {
@@ -604,10 +557,10 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restri
     }
   }
   __syncthreads();
-  if (nparts > 0 && tid < n) {
-    Acc<T> acc = scr[tid];
-    for (int q = 1; q < nparts; ++q) acc.merge(scr[q * n + tid]);
-    out_z[tid] = acc.value() + add_z(tid);
+  for (int j = tid; j < n; j += NTHREADS) {
+    Acc<T> acc = scr[j];
+    for (int q = 1; q < nparts; ++q) acc.merge(scr[q * 4 * nq + j]);
+    out_z[j] = acc.value() + add_z(j);
   }
   __syncthreads();
 }

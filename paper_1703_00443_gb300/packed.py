@@ -73,13 +73,18 @@ class PackedBatch:
 
     # ---------------------------------------------------------------- packing helpers
     def pack_vec(self, items, key):
-        """Concatenate per-instance arrays (any shape, row-major) for buffer ``key``."""
-        flat = [torch.as_tensor(x).reshape(-1) for x in items]
-        if not flat or self.totals[key] == 0:
-            return torch.zeros(max(self.totals[key], 1), dtype=self.dtype, device=self.device)
-        out = torch.cat([f.to(device=self.device, dtype=self.dtype) for f in flat])
-        if out.numel() != self.totals[key]:
-            raise QPError(f"packed {key} has {out.numel()} elements, expected {self.totals[key]}")
+        """Place per-instance arrays (any shape, row-major) at their planned offsets in a flat
+        buffer for ``key`` (offsets are padded to 4 elements; the gaps hold zeros)."""
+        out = torch.zeros(max(self.totals[key], 1), dtype=self.dtype, device=self.device)
+        items = list(items)
+        if len(items) != self.B:
+            raise QPError(f"{len(items)} items for {self.B} instances")
+        for o, l, x in zip(self.offsets[key], self.lengths[key], items):
+            t = torch.as_tensor(x).reshape(-1)
+            if t.numel() != l:
+                raise QPError(f"{key}: instance has {t.numel()} elements, expected {l}")
+            if l:
+                out[o:o + l] = t.to(device=self.device, dtype=self.dtype)
         return out
 
     def pack(self, instances):
@@ -98,10 +103,10 @@ class PackedBatch:
     def forward(self, Q, q, G, h, A, b, out=None) -> PackedForward:
         lib = _lib.load()
         dev = self.device
-        if out is None:
-            z = torch.empty(max(self.totals["q"], 1), dtype=self.dtype, device=dev)
-            lam = torch.empty(max(self.totals["h"], 1), dtype=self.dtype, device=dev)
-            nu = torch.empty(max(self.totals["b"], 1), dtype=self.dtype, device=dev)
+        if out is None:   # zero-filled so the padding gaps between instances are defined
+            z = torch.zeros(max(self.totals["q"], 1), dtype=self.dtype, device=dev)
+            lam = torch.zeros(max(self.totals["h"], 1), dtype=self.dtype, device=dev)
+            nu = torch.zeros(max(self.totals["b"], 1), dtype=self.dtype, device=dev)
             status = torch.empty(max(self.B, 1), dtype=torch.int32, device=dev)
             iters = torch.empty(max(self.B, 1), dtype=torch.int32, device=dev)
             resid = torch.empty((max(self.B, 1), 4), dtype=torch.float64, device=dev)
@@ -121,7 +126,7 @@ class PackedBatch:
         lib = _lib.load()
         dev = self.device
         if out is None:
-            out = tuple(torch.empty(max(self.totals[k], 1), dtype=self.dtype, device=dev)
+            out = tuple(torch.zeros(max(self.totals[k], 1), dtype=self.dtype, device=dev)
                         for k in self.KEYS)
         with torch.cuda.device(dev):
             rc = lib.qp_backward_packed(

@@ -103,6 +103,8 @@ def test_packed_cuda_graph_replay_matches_eager():
         fout.z.zero_()
         graph.replay()
         torch.cuda.synchronize()
-        assert torch.equal(fout.z, ez)
-        for a, b in zip(gout, egrads):
+        for a, b in zip(pb.unpack(fout.z, "q"), pb.unpack(ez, "q")):
             assert torch.equal(a, b)
+        for key, a, b in zip(pb.KEYS, gout, egrads):
+            for x, y in zip(pb.unpack(a, key), pb.unpack(b, key)):
+                assert torch.equal(x, y), key
