@@ -174,6 +174,35 @@ def cpu_baseline(n, p, m, budget_s=15.0, gpu_out=None):
     return res, acc
 
 
+def serving_run(dev, rate, count):
+    """Poisson stream of fwd+bwd requests (n log-uniform in [16, 512], nineq = n, neq = n/4)
+    through the continuous-batching server; p50/p99 latency from arrival to result."""
+    import torch
+    from paper_1703_00443_gb300 import inputs
+    from paper_1703_00443_gb300.serving import QPServer, poisson_run
+    sizes = inputs.serve_sizes(128)
+    pool = []
+    for i, (nn, pp, mm) in enumerate(sizes):
+        data = inputs.random_qp(nn, pp, mm, workload=inputs.WL_SERVE, index=i)
+        gg = inputs.upstream_grad(1, nn, workload=inputs.WL_SERVE, start=i)[0]
+        pool.append((tuple(np.float32(x) for x in data), np.float32(gg)))
+    server = QPServer(device=dev, max_inflight=4, max_batch=512)
+    try:
+        poisson_run(server, pool[:16], rate, min(64, count))       # warm-up
+        server.latencies.clear()
+        server.batch_sizes.clear()
+        server.completed = 0
+        results, wall = poisson_run(server, pool, rate, count, seed=1)
+        st = server.stats()
+    finally:
+        server.close()
+    bad = sum(r["status"] != 0 for r in results)
+    return {"rate_req_s": rate, "requests": count, "throughput_req_s": count / wall,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"],
+            "mean_batch": st["mean_batch"], "nonconverged": int(bad),
+            "workload": "n log-uniform [16,512], nineq=n, neq=n/4, fwd+bwd, host arrays in/out"}
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -292,6 +321,29 @@ def run_gpu(args):
             e2e_ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
 
+    # The same 128 instances through the packed (persistent, uneven-capable) path.
+    packed_ms = None
+    if not args.no_extras:
+        from paper_1703_00443_gb300.packed import PackedBatch
+        pb = PackedBatch([(n, p, m)] * B, device=dev)
+        Pq = [pb.pack_vec([x[i] for i in range(B)], k) for x, k in
+              zip((batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b), pb.KEYS)]
+        Pg = pb.pack_vec([g[i] for i in range(B)], "q")
+        fo = pb.forward(*Pq)
+        go = pb.backward(Pq[0], Pq[2], Pq[4], Pg)
+        torch.cuda.synchronize()
+        pms = []
+        for k in range(max(10, args.steps // 5)):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.forward(*Pq, out=fo)
+            pb.backward(Pq[0], Pq[2], Pq[4], Pg, out=go)
+            e1.record(stream)
+            e1.synchronize()
+            pms.append(e0.elapsed_time(e1))
+        packed_ms = statistics.mean(pms)
+
     # Max over ranks.
     tvec = torch.tensor([step_ms, sum(fwd_ms) / args.steps, statistics.mean(e2e_ms)], device=dev,
                         dtype=torch.float64)
@@ -312,6 +364,9 @@ def run_gpu(args):
     achieved = f_fwd * B / (fwd_mean / 1e3) / 1e12
     gpu_out = {"z": z.cpu().numpy(), "dq": gout[1].cpu().numpy(), "dG": gout[2].cpu().numpy(),
                "dQ": gout[0].cpu().numpy()}
+    served = None
+    if not args.no_extras and ws == 1:
+        served = serving_run(dev, args.serve_rate, args.serve_count)
     cpu, acc = (None, None)
     if not args.no_cpu_baseline and ws == 1:
         cpu, acc = cpu_baseline(n, p, m, budget_s=args.cpu_budget, gpu_out=gpu_out)
@@ -336,6 +391,10 @@ def run_gpu(args):
                      "algorithmic_flops_per_launch": f_fwd * B},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
+        "batched_vs_plain": None if packed_ms is None else {
+            "plain_fixed_size_ms_per_step": step_ms, "packed_persistent_ms_per_step": packed_ms,
+            "note": "same 128 instances; packed = one persistent launch per direction over descriptors"},
+        "served": served,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "accuracy_vs_oracle": acc,
@@ -355,6 +414,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the packed and serving runs")
+    ap.add_argument("--serve-rate", type=float, default=5000.0)
+    ap.add_argument("--serve-count", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

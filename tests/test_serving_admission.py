@@ -1,0 +1,37 @@
+"""Host logic of the serving loop's admission policy (no GPU needed)."""
+import collections
+from types import SimpleNamespace
+
+from paper_1703_00443_gb300.serving import Admission
+
+
+def _q(sizes):
+    return collections.deque(SimpleNamespace(nbytes=s, name=i) for i, s in enumerate(sizes))
+
+
+def test_fifo_batches_respect_budget_and_cap():
+    adm = Admission(budget_bytes=100, max_batch=3)
+    q = _q([30, 30, 30, 30, 50])
+    b1, rej, t1 = adm.take(q)
+    assert [r.name for r in b1] == [0, 1, 2] and not rej and t1 == 90   # cap of 3
+    b2, rej, t2 = adm.take(q)
+    assert b2 == [] and adm.reserved == 90                              # budget exhausted
+    adm.release(t1)
+    b3, rej, t3 = adm.take(q)
+    assert [r.name for r in b3] == [3, 4] and t3 == 80
+
+
+def test_oversized_request_is_rejected_not_blocking():
+    adm = Admission(budget_bytes=100, max_batch=8)
+    q = _q([150, 20, 20])
+    b, rej, t = adm.take(q)
+    assert [r.name for r in rej] == [0]
+    assert [r.name for r in b] == [1, 2] and t == 40
+
+
+def test_fifo_order_is_kept_when_head_does_not_fit():
+    adm = Admission(budget_bytes=100, max_batch=8)
+    adm.reserved = 70
+    q = _q([50, 10])
+    b, rej, t = adm.take(q)
+    assert b == [] and len(q) == 2      # the head waits; nothing overtakes it
