@@ -56,15 +56,15 @@ typedef struct qp_options {
   double  mu_tol;    /* ... and μ = sᵀλ/nineq ≤ mu_tol                                */
   int32_t max_iter;  /* bound on Newton steps of the interior point loop               */
   int32_t refine;    /* most FP64 iterative-refinement steps of the backward KKT solve
-                        (0-4): one always, more while the FP64 residual is above
-                        1e-9·(1 + ‖∂ℓ/∂z*‖∞)                                        */
+                        (0-4); refinement stops once a correction is below 1e-3 of the
+                        solution (one step for well-conditioned systems)              */
   int32_t path;      /* 0: automatic kernel choice; 1: always the global-memory kernel.
                         Forward and backward of one batch must use the same value.      */
   int32_t reserved;  /* set to 0                                                        */
 } qp_options;
 
-/* Default options for a dtype (QP_F32: tol 1e-10, mu_tol 1e-11, max_iter 50, refine 3;
- * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 3; path 0). */
+/* Default options for a dtype (QP_F32: tol 1e-10, mu_tol 1e-11, max_iter 50, refine 4;
+ * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 4; path 0). */
 void qp_default_options(int dtype, qp_options* opt);
 
 /* Bytes of workspace qp_forward needs for B instances of one size (0 on invalid sizes),

@@ -151,7 +151,7 @@ void qp_default_options(int dtype, qp_options* opt) {
     opt->mu_tol = 1e-11;
     opt->max_iter = 50;
   }
-  opt->refine = 3;
+  opt->refine = 4;
   opt->path = 0;
   opt->reserved = 0;
 }

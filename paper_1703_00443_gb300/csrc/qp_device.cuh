@@ -1485,18 +1485,12 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   __syncthreads();
 
   // Iterative refinement with the FP64-accurate residual of the reduced system
-  //   ρ_z = Q d_z + Gᵀ d̃_λ + Aᵀ d_ν + ∂ℓ/∂z,  ρ_λ = G d_z − D(s/λ) d̃_λ,  ρ_ν = A d_z:
-  // at least one correction, then further ones (at most P.refine in all) while
-  // ‖ρ‖∞ > 1e-9·(1 + ‖∂ℓ/∂z‖∞).  Ill-conditioned equality blocks (A Q⁻¹ Aᵀ near singular)
-  // need the extra steps; well-conditioned ones stop after the first.
-  float gmax;
-  {
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)gz[i]));
-    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
-    gmax = v[0];
-  }
-  const float rthr = 1e-9f * (1.f + gmax);
+  //   ρ_z = Q d_z + Gᵀ d̃_λ + Aᵀ d_ν + ∂ℓ/∂z,  ρ_λ = G d_z − D(s/λ) d̃_λ,  ρ_ν = A d_z.
+  // With a factorisation of relative accuracy δ the correction shrinks by about κδ per
+  // step and ‖correction_k‖/‖d‖ estimates that rate, so the error left after a step is
+  // about ‖correction‖/‖d‖ times the correction: refinement stops once a correction is
+  // below 1e-3·‖d‖∞ (at most P.refine steps).  Well-conditioned systems stop after the first
+  // step; near-singular A Q⁻¹ Aᵀ blocks take more.
   for (int rs = 0; rs < P.refine; ++rs) {
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
@@ -1504,14 +1498,6 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, 4 * NTHREADS, [&](int j) { return (double)gz[j]; },
                  [&](int i) { return -(s[i] / lam[i]) * dlt[i]; }, [&](int) { return 0.0; },
                  rz, rl, rn);
-    if (rs > 0) {
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
-      for (int i = tid; i < p; i += NTHREADS) v[1] = ropf<R_MAX>(v[1], fabsf((float)rl[i]));
-      for (int i = tid; i < m; i += NTHREADS) v[2] = ropf<R_MAX>(v[2], fabsf((float)rn[i]));
-      block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
-      if (v[0] <= rthr && v[1] <= rthr && v[2] <= rthr) break;
-    }
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
     __syncthreads();
     mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
@@ -1524,10 +1510,24 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     if (p == 0)
       for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
     __syncthreads();
-    for (int i = tid; i < n; i += NTHREADS) dz[i] += (double)dzn[i];
-    for (int i = tid; i < m; i += NTHREADS) dnu[i] += (double)dzn[nz + i];
-    for (int i = tid; i < p; i += NTHREADS) dlt[i] += (double)dl[i];
-    __syncthreads();
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n; i += NTHREADS) {
+      dz[i] += (double)dzn[i];
+      v[0] = ropf<R_MAX>(v[0], fabsf((float)dzn[i]));
+      v[1] = ropf<R_MAX>(v[1], fabsf((float)dz[i]));
+    }
+    for (int i = tid; i < m; i += NTHREADS) {
+      dnu[i] += (double)dzn[nz + i];
+      v[0] = ropf<R_MAX>(v[0], fabsf((float)dzn[nz + i]));
+      v[1] = ropf<R_MAX>(v[1], fabsf((float)dnu[i]));
+    }
+    for (int i = tid; i < p; i += NTHREADS) {
+      dlt[i] += (double)dl[i];
+      v[0] = ropf<R_MAX>(v[0], fabsf((float)dl[i]));
+      v[1] = ropf<R_MAX>(v[1], fabsf((float)dlt[i]));
+    }
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
+    if (!(v[0] > 1e-3f * v[1])) break;   // also stops on NaN
   }
 
   // Gradients of Eq. 8 with d̃_λ = D(λ*) d_λ, formed in the factor precision T from

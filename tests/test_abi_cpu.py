@@ -28,7 +28,7 @@ def test_host_side_queries():
     lib = _lib.load()
     o = _lib.QPOptions()
     lib.qp_default_options(0, ctypes.byref(o))
-    assert o.max_iter == 50 and o.refine == 3 and o.path == 0 and 0 < o.tol < 1e-6
+    assert o.max_iter == 50 and o.refine == 4 and o.path == 0 and 0 < o.tol < 1e-6
     lib.qp_default_options(1, ctypes.byref(o))
     assert o.max_iter == 100 and o.tol <= 1e-12
     assert lib.qp_workspace_bytes(0, 128, 100, 100, 50) >= 128 * (250 * 150 + 100 * 100) * 4
