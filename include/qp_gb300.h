@@ -56,8 +56,9 @@ typedef struct qp_options {
   double  mu_tol;    /* ... and μ = sᵀλ/nineq ≤ mu_tol                                */
   int32_t max_iter;  /* bound on Newton steps of the interior point loop               */
   int32_t refine;    /* most FP64 iterative-refinement steps of the backward KKT solve
-                        (0-4); refinement stops once a correction is below 1e-3 of the
-                        solution (one step for well-conditioned systems)              */
+                        (0-4); refinement stops once each block of the correction is
+                        below 1e-3 of its block of the solution (floored at 1e-6 of
+                        ‖∂ℓ/∂z*‖∞): one step for well-conditioned systems            */
   int32_t path;      /* 0: automatic kernel choice; 1: always the global-memory kernel.
                         Forward and backward of one batch must use the same value.      */
   int32_t reserved;  /* set to 0                                                        */

@@ -1488,9 +1488,17 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   //   ρ_z = Q d_z + Gᵀ d̃_λ + Aᵀ d_ν + ∂ℓ/∂z,  ρ_λ = G d_z − D(s/λ) d̃_λ,  ρ_ν = A d_z.
   // With a factorisation of relative accuracy δ the correction shrinks by about κδ per
   // step and ‖correction_k‖/‖d‖ estimates that rate, so the error left after a step is
-  // about ‖correction‖/‖d‖ times the correction: refinement stops once a correction is
-  // below 1e-3·‖d‖∞ (at most P.refine steps).  Well-conditioned systems stop after the first
-  // step; near-singular A Q⁻¹ Aᵀ blocks take more.
+  // about that ratio times the correction: refinement stops once, in each of the three
+  // blocks (d_z, d_ν, d̃_λ), the correction is below 1e-3·max(‖block‖∞, 1e-3·‖∂ℓ/∂z‖∞)
+  // (at most P.refine steps).  Well-conditioned systems stop after the first step;
+  // near-singular A Q⁻¹ Aᵀ blocks take more.
+  float gfloor;
+  {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)gz[i]));
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
+    gfloor = 1e-3f * v[0];
+  }
   for (int rs = 0; rs < P.refine; ++rs) {
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
@@ -1510,24 +1518,28 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     if (p == 0)
       for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
     __syncthreads();
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    float v[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
     for (int i = tid; i < n; i += NTHREADS) {
       dz[i] += (double)dzn[i];
       v[0] = ropf<R_MAX>(v[0], fabsf((float)dzn[i]));
-      v[1] = ropf<R_MAX>(v[1], fabsf((float)dz[i]));
+      w[0] = ropf<R_MAX>(w[0], fabsf((float)dz[i]));
     }
     for (int i = tid; i < m; i += NTHREADS) {
       dnu[i] += (double)dzn[nz + i];
-      v[0] = ropf<R_MAX>(v[0], fabsf((float)dzn[nz + i]));
-      v[1] = ropf<R_MAX>(v[1], fabsf((float)dnu[i]));
+      v[1] = ropf<R_MAX>(v[1], fabsf((float)dzn[nz + i]));
+      w[1] = ropf<R_MAX>(w[1], fabsf((float)dnu[i]));
     }
     for (int i = tid; i < p; i += NTHREADS) {
       dlt[i] += (double)dl[i];
-      v[0] = ropf<R_MAX>(v[0], fabsf((float)dl[i]));
-      v[1] = ropf<R_MAX>(v[1], fabsf((float)dlt[i]));
+      v[2] = ropf<R_MAX>(v[2], fabsf((float)dl[i]));
+      w[2] = ropf<R_MAX>(w[2], fabsf((float)dlt[i]));
     }
     block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
-    if (!(v[0] > 1e-3f * v[1])) break;   // also stops on NaN
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(w, red);
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) done = done && (v[k] <= 1e-3f * fmaxf(w[k], gfloor));
+    if (done || !isfinite(v[0] + v[1] + v[2])) break;
   }
 
   // Gradients of Eq. 8 with d̃_λ = D(λ*) d_λ, formed in the factor precision T from
