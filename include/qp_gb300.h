@@ -172,6 +172,27 @@ int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instanc
                        const void* dl_dz, void* dQ, void* dq, void* dG, void* dh, void* dA,
                        void* db, void* stream);
 
+/*
+ * qp_forward_noalloc -- qp_forward for callers that cannot allocate device memory (a control
+ * loop with a hard latency budget, a process whose device memory is fixed when it starts, a
+ * plugin whose host framework owns all allocation).  The paper has no counterpart: this is an
+ * interface variant, not part of the method.
+ *
+ * Same arguments and results as qp_forward, but no workspace: the library's own file-scope
+ * device array of QP_NOALLOC_SCRATCH_BYTES bytes (32 MiB, held by every device that loads the
+ * library until exit) takes its place.  It allocates nothing.  Returns QP_ENOSPACE when
+ * qp_workspace_bytes_opt() for the call exceeds QP_NOALLOC_SCRATCH_BYTES (e.g. about 170
+ * instances of n = 100, nineq = 100, neq = 50 in FP32).  The first call on a device looks up
+ * the array's address there (make it before any stream capture).  All calls share the
+ * array, so calls that overlap on the GPU race; its contents after a call are that call's
+ * factorisation, which is not reachable from qp_backward.
+ */
+#define QP_NOALLOC_SCRATCH_BYTES (32u << 20)
+int qp_forward_noalloc(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+                       const void* Q, const void* q, const void* G, const void* h,
+                       const void* A, const void* b, void* z, void* lam, void* nu,
+                       int32_t* status, int32_t* iters, double* resid, void* stream);
+
 /* Human-readable text for a QP_E* code. */
 const char* qp_strerror(int code);
 
