@@ -52,6 +52,37 @@ def algorithmic_bytes(n, p, m, esz=4):
     return fwd_in + fwd_out + bwd
 
 
+def kernel_source_sha256():
+    import glob
+    import hashlib
+    files = sorted(glob.glob(os.path.join(HERE, "paper_1703_00443_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(HERE, "paper_1703_00443_gb300", "csrc", "*.cuh")))
+    h = hashlib.sha256()
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(summary="qp_fwd_kernel_n100_b128.md"):
+    """DRAM bytes per launch from the committed ncu summary, or None when the kernel sources
+    changed since that capture (the summary records their hash)."""
+    path = os.path.join(HERE, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "source_sha256"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != kernel_source_sha256():
+        return None
+    try:
+        return int(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -387,7 +418,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": "qp_fwd_kernel", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                     "traffic": None,
+                     "traffic": profiled_traffic(),
+                     "traffic_unit": "bytes per launch (dram read+write, ncu)",
                      "algorithmic_flops_per_launch": f_fwd * B},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
@@ -405,6 +437,104 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def _time_fixed(Tin, gdev, steps, flush, stream):
+    """Mean device time (ms) of one fwd+bwd step of the fixed-size path (L2 flushed)."""
+    import torch
+    from paper_1703_00443_gb300 import qp_backward, qp_forward
+    f = qp_forward(*Tin)
+    go = qp_backward(f, gdev)
+    for _ in range(2):
+        f = qp_forward(*Tin, workspace=f.workspace, out=(f.z, f.lam, f.nu, f.status, f.iters, f.resid))
+        qp_backward(f, gdev, out=go)
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = qp_forward(*Tin, workspace=f.workspace, out=(f.z, f.lam, f.nu, f.status, f.iters, f.resid))
+        qp_backward(f, gdev, out=go)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms), f
+
+
+def run_workload(args):
+    """Secondary workloads, one JSON line each (not the headline metric)."""
+    import torch
+    from paper_1703_00443_gb300 import inputs
+    from paper_1703_00443_gb300.packed import PackedBatch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    line = {"workload": args.workload, "unit": UNIT, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "l2": "flushed between timed steps"}
+    if args.workload == "sweep":
+        rows = []
+        for n in (10, 50, 100, 500):
+            for B in (1, 64, 128):
+                p, m = n, n // 2
+                bt = inputs.random_batch(B, n, p, m, workload=inputs.WL_SWEEP)
+                g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
+                Tin = [torch.from_numpy(x).to(dev) for x in (bt.Q, bt.q, bt.G, bt.h, bt.A, bt.b)]
+                steps = 5 if n == 500 else 20
+                ms, f = _time_fixed(Tin, torch.from_numpy(g).to(dev), steps, flush, stream)
+                rows.append({"n": n, "nineq": p, "neq": m, "batch": B, "ms_per_step": ms,
+                             "solves_per_s": B / (ms / 1e3),
+                             "iters_mean": float(f.iters.float().mean()),
+                             "converged": int((f.status == 0).sum())})
+        line.update({"metric": "QP fwd+bwd solves/sec, timing sweep (n, nineq=n, neq=n/2)",
+                     "sweep": rows})
+    elif args.workload == "onehot":
+        B, n, m = 512, 64, 40
+        bt = inputs.onehot_batch(B, n, m)
+        tgt = torch.from_numpy(inputs.onehot_target(B, n)).to(dev)
+        Tin = [torch.from_numpy(x).to(dev) for x in (bt.Q, bt.q, bt.G, bt.h, bt.A, bt.b)]
+        from paper_1703_00443_gb300 import qp_forward
+        z = qp_forward(*Tin).z
+        gdev = (2.0 / n) * (z - tgt)
+        ms, f = _time_fixed(Tin, gdev, 20, flush, stream)
+        line.update({"metric": "structured one-hot QP fwd+bwd solves/sec (n=64, neq=40, z>=0, batch 512)",
+                     "value": B / (ms / 1e3), "ms_per_step": ms,
+                     "iters_mean": float(f.iters.float().mean()), "converged": int((f.status == 0).sum())})
+    elif args.workload == "uneven":
+        count = args.uneven_count
+        sizes = inputs.uneven_sizes(count)
+        pb = PackedBatch(sizes, device=dev)
+        # per-instance data generated on the host (seeded, independent of the batch)
+        inst = [inputs.random_qp(nn, pp, mm, workload=inputs.WL_UNEVEN, index=i)
+                for i, (nn, pp, mm) in enumerate(sizes)]
+        gl = [inputs.upstream_grad(1, nn, workload=inputs.WL_UNEVEN, start=i)[0]
+              for i, (nn, pp, mm) in enumerate(sizes)]
+        P = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
+        G1 = pb.pack_vec([np.float32(x) for x in gl], "q")
+        fo = pb.forward(*P)
+        go = pb.backward(P[0], P[2], P[4], G1)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.uneven_steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.forward(*P, out=fo)
+            pb.backward(P[0], P[2], P[4], G1, out=go)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.mean(ms)
+        st = fo.status[:count].cpu().numpy()
+        line.update({"metric": "uneven batch fwd+bwd solves/sec (one persistent launch each way)",
+                     "value": count / (t / 1e3), "ms_per_step": t, "count": count,
+                     "global_path_instances": pb.n_global,
+                     "workspace_gb": int(pb.sizes.ws_bytes) / 1e9,
+                     "iters_mean": float(fo.iters[:count].float().mean()),
+                     "converged": int((st == 0).sum()),
+                     "sizes": "n~U{8..256}, nineq~U{n/2..2n}, neq~U{0..n/4}"})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,9 +547,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the packed and serving runs")
     ap.add_argument("--serve-rate", type=float, default=5000.0)
     ap.add_argument("--serve-count", type=int, default=1000)
+    ap.add_argument("--workload", default="headline", choices=["headline", "sweep", "onehot", "uneven"])
+    ap.add_argument("--uneven-count", type=int, default=4096)
+    ap.add_argument("--uneven-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "headline":
+        run_workload(args)
     else:
         run_gpu(args)
 

@@ -34,10 +34,10 @@ int tiles_of(int N) {
   return NT * (NT + 1) / 2;
 }
 
-// Smallest compiled (SW, CH) variant whose register tiles cover the sweep matrix of order
-// n + neq + nineq and the nineq×nineq Schur complement.
+// Smallest compiled (SW, CH) variant whose register tiles cover the sweep matrix (order
+// nz + neq + nineq, with nz the padded variable count) and the nineq×nineq Schur complement.
 bool pick_variant(int dtype, int n, int nineq, int neq, int* SW, int* CH) {
-  const int t3 = tiles_of(n + neq + nineq), tp = tiles_of(nineq);
+  const int t3 = tiles_of(qpk::padded_nz(n, neq) + neq + nineq), tp = tiles_of(nineq);
   const int sws[3] = {1, 2, 4};
   const int esz = dtype == QP_F32 ? 4 : 8;
   for (int ch = 1; ch <= 2; ++ch) {

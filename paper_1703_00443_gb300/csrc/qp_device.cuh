@@ -676,6 +676,7 @@ __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restric
   const int tid = threadIdx.x;
   const int nz = padded_nz(n, m), m1 = nz + m, N = m1 + p;
   const int NT = (N + 3) >> 2, ntiles = NT * (NT + 1) / 2, KB = m1 >> 2;
+  if (ntiles > SW * NTHREADS) return false;   // register tiles too few (host plans avoid it)
   // cb layout per parity: Ĉ panel [16·NT], Ĉ·D⁻¹ panel [16·NT], pivot rows R [16]; flags.
   const int pstride = 32 * NT + 16;
   int* flag = reinterpret_cast<int*>(cb + 2 * pstride);
@@ -826,6 +827,7 @@ template <typename T, int CH>
 __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const T* dsh, T* cb) {
   const int tid = threadIdx.x;
   const int NT = (p + 3) >> 2, ntiles = NT * (NT + 1) / 2;
+  if (ntiles > CH * NTHREADS) return false;   // register tiles too few (host plans avoid it)
   // cb layout per parity: L panel [16·NT], X block row [16·NT], Linv [16]; flags after.
   const int pstride = 32 * NT + 16;
   int* flag = reinterpret_cast<int*>(cb + 2 * pstride);

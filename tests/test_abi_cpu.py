@@ -54,3 +54,23 @@ def test_invalid_arguments_rejected_before_launch():
     assert lib.qp_forward(null, 0, 1, 4, 2, 0, *([null] * 13), 0, null) == 1
     assert lib.qp_forward(null, 0, 0, 4, 2, 0, *([null] * 13), 0, null) == 0   # empty batch
     assert lib.qp_backward(null, 0, 1, 4, 2, 0, *([null] * 4), 0, *([null] * 8)) == 1
+
+
+def test_register_tile_capacity_includes_padding():
+    """The shared-memory path is only chosen when the padded sweep matrix fits the register
+    tiles (4×4 tiles, at most 4 slots of 512 threads; 2 slots for the Schur complement)."""
+    lib = _lib.load()
+
+    def tiles(N):
+        nt = (N + 3) // 4
+        return nt * (nt + 1) // 2
+
+    for n in range(60, 200, 7):
+        for p in range(40, 200, 9):
+            for m in (0, 3, 8, n // 4):
+                if m > n:
+                    continue
+                nz = n + (4 - (n + m) % 4) % 4
+                fits = tiles(nz + m + p) <= 4 * 512 and tiles(p) <= 2 * 512
+                if lib.qp_uses_global_path(0, n, p, m) == 0:
+                    assert fits, (n, p, m)

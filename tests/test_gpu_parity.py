@@ -108,7 +108,8 @@ def test_onehot_structured():
 
 
 @pytest.mark.parametrize("n,nineq,neq", [(7, 13, 3), (1, 2, 0), (5, 0, 2), (12, 0, 0),
-                                         (33, 9, 0), (60, 170, 10), (3, 1, 1)])
+                                         (33, 9, 0), (60, 170, 10), (3, 1, 1),
+                                         (135, 109, 8), (87, 157, 8)])
 def test_ragged_and_edge_sizes(n, nineq, neq):
     B = 5
     assert supported(torch.float32, n, nineq, neq)
