@@ -502,7 +502,11 @@ def run_workload(args):
     elif args.workload == "uneven":
         count = args.uneven_count
         sizes = inputs.uneven_sizes(count)
-        pb = PackedBatch(sizes, device=dev)
+        tuning = None
+        if args.tuned:
+            from paper_1703_00443_gb300 import autotune
+            tuning = autotune.autotune(device=dev)
+        pb = PackedBatch(sizes, device=dev, tuning=tuning)
         # per-instance data generated on the host (seeded, independent of the batch)
         inst = [inputs.random_qp(nn, pp, mm, workload=inputs.WL_UNEVEN, index=i)
                 for i, (nn, pp, mm) in enumerate(sizes)]
@@ -528,6 +532,7 @@ def run_workload(args):
         line.update({"metric": "uneven batch fwd+bwd solves/sec (one persistent launch each way)",
                      "value": count / (t / 1e3), "ms_per_step": t, "count": count,
                      "global_path_instances": pb.n_global,
+                     "tuned": bool(args.tuned),
                      "workspace_gb": int(pb.sizes.ws_bytes) / 1e9,
                      "iters_mean": float(fo.iters[:count].float().mean()),
                      "converged": int((st == 0).sum()),
@@ -550,6 +555,7 @@ def main():
     ap.add_argument("--workload", default="headline", choices=["headline", "sweep", "onehot", "uneven"])
     ap.add_argument("--uneven-count", type=int, default=4096)
     ap.add_argument("--uneven-steps", type=int, default=3)
+    ap.add_argument("--tuned", action="store_true", help="autotune the packed schedule first")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

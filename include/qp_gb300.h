@@ -156,6 +156,14 @@ typedef struct qp_packed_sizes {
 int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
                    qp_instance_desc* desc, qp_packed_sizes* sizes);
 
+/* qp_packed_plan with per-instance hints from a tuner: path_hint[i] (may be NULL) is 0 for
+ * the automatic choice, 1 for the global-memory kernel, 2 for the shared-memory kernel
+ * (QP_EUNSUPPORTED if it cannot take that size); cost[i] (may be NULL) replaces the built-in
+ * cost estimate that orders the work queue (largest first). */
+int qp_packed_plan_ex(const qp_options* opt, int dtype, int B, const int32_t* dims,
+                      const int8_t* path_hint, const float* cost, qp_instance_desc* desc,
+                      qp_packed_sizes* sizes);
+
 /* Forward pass of a packed batch (device pointers as in qp_forward, packed as above;
  * status/iters/resid indexed by instance id; workspace of sizes->ws_bytes bytes). */
 int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,

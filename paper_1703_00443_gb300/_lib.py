@@ -107,6 +107,9 @@ EXPORTS = {
                            + [c_void_p] * 12 + [c_void_p]),
     "qp_packed_plan": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,
                                ctypes.POINTER(QPInstanceDesc), ctypes.POINTER(QPPackedSizes)]),
+    "qp_packed_plan_ex": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p, c_void_p,
+                                  c_void_p, ctypes.POINTER(QPInstanceDesc),
+                                  ctypes.POINTER(QPPackedSizes)]),
     "qp_forward_packed": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,
                                   ctypes.POINTER(QPPackedSizes)] + [c_void_p] * 13 + [c_size_t, c_void_p]),
     "qp_backward_packed": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,

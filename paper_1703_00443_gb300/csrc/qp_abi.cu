@@ -85,13 +85,16 @@ struct Plan {
   size_t fsmem = 0, bsmem = 0, ws = 0;
 };
 
+// force: 0 automatic, 1 global-memory path, 2 shared-memory path (ok = false if impossible).
 Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
   Plan pl;
   const size_t lim = (size_t)max_smem_optin();
   int sw = 0, ch = 0;
   const int nz4 = qpk::padded_nz(n, neq);
-  if (!force_global && pick_variant(dtype, n, nineq, neq, &sw, &ch) &&
-      fwd_smem(dtype, n, nz4, nineq, neq, false) <= lim) {
+  const bool smem_ok = pick_variant(dtype, n, nineq, neq, &sw, &ch) &&
+                       fwd_smem(dtype, n, nz4, nineq, neq, false) <= lim;
+  if (force_global == 2 && !smem_ok) return pl;
+  if (force_global != 1 && smem_ok) {
     pl.large = false;
     pl.sw = sw;
     pl.ch = ch;
@@ -254,6 +257,12 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
 
 int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
                    qp_instance_desc* desc, qp_packed_sizes* sizes) {
+  return qp_packed_plan_ex(opt, dtype, B, dims, nullptr, nullptr, desc, sizes);
+}
+
+int qp_packed_plan_ex(const qp_options* opt, int dtype, int B, const int32_t* dims,
+                      const int8_t* path_hint, const float* cost, qp_instance_desc* desc,
+                      qp_packed_sizes* sizes) {
   if ((dtype != QP_F32 && dtype != QP_F64) || B < 0 || !sizes || (B > 0 && (!dims || !desc)))
     return QP_EINVAL;
   qp_options o;
@@ -268,7 +277,9 @@ int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
   for (int i = 0; i < B; ++i) {
     const int n = dims[3 * i], p = dims[3 * i + 1], m = dims[3 * i + 2];
     if (!dims_ok(1, n, p, m)) return QP_EINVAL;
-    const Plan pl = make_plan(dtype, n, p, m, o.path);
+    const int hint = path_hint ? path_hint[i] : 0;
+    if (hint < 0 || hint > 2) return QP_EINVAL;
+    const Plan pl = make_plan(dtype, n, p, m, hint ? hint : o.path);
     if (!pl.ok) return QP_EUNSUPPORTED;
     qp_instance_desc& d = desc[i];
     d.n = n; d.nineq = p; d.neq = m; d.id = i; d.nz = pl.nz; d.flags = pl.large ? 1 : 0;
@@ -287,7 +298,7 @@ int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
     }
     fsm = std::max(fsm, pl.fsmem);
     bsm = std::max(bsm, pl.bsmem);
-    order.push_back({est_cost(n, pl.nz, p, m, pl.large), i});
+    order.push_back({cost ? (double)cost[i] : est_cost(n, pl.nz, p, m, pl.large), i});
   }
   // Register-tile variant covering every shared-memory-path instance.
   int sw = 0, ch = 0;

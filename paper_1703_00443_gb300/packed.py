@@ -36,7 +36,7 @@ class PackedBatch:
 
     KEYS = ("Q", "q", "G", "h", "A", "b")
 
-    def __init__(self, dims, dtype=torch.float32, device="cuda", options=None):
+    def __init__(self, dims, dtype=torch.float32, device="cuda", options=None, tuning=None):
         self.dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
         self.B = self.dims.shape[0]
         self.dtype = dtype
@@ -46,9 +46,15 @@ class PackedBatch:
         lib = _lib.load()
         self.desc_host = (_lib.QPInstanceDesc * max(self.B, 1))()
         self.sizes = _lib.QPPackedSizes()
-        rc = lib.qp_packed_plan(ctypes.byref(self.options), self.code, self.B,
-                                self.dims.ctypes.data_as(ctypes.c_void_p), self.desc_host,
-                                ctypes.byref(self.sizes))
+        hints = cost = None
+        if tuning is not None:
+            # per-instance kernel path and predicted time from a measured tuning table
+            hints, cost = tuning.plan_arrays(self.dims)
+        rc = lib.qp_packed_plan_ex(ctypes.byref(self.options), self.code, self.B,
+                                   self.dims.ctypes.data_as(ctypes.c_void_p),
+                                   None if hints is None else hints.ctypes.data_as(ctypes.c_void_p),
+                                   None if cost is None else cost.ctypes.data_as(ctypes.c_void_p),
+                                   self.desc_host, ctypes.byref(self.sizes))
         _check(rc)
         raw = bytes(memoryview(self.desc_host))[: self.B * ctypes.sizeof(_lib.QPInstanceDesc)]
         self.desc = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(self.device) \

@@ -108,3 +108,26 @@ def test_packed_cuda_graph_replay_matches_eager():
         for key, a, b in zip(pb.KEYS, gout, egrads):
             for x, y in zip(pb.unpack(a, key), pb.unpack(b, key)):
                 assert torch.equal(x, y), key
+
+
+def test_autotuned_packed_batch_matches_alone_on_the_chosen_path():
+    from paper_1703_00443_gb300 import autotune, default_options
+    classes = [(16, 16, 4), (64, 64, 16), (96, 192, 0)]
+    tun = autotune.autotune(device=DEV, classes=classes, save_to=None)
+    sizes = [(16, 16, 4), (64, 64, 16), (96, 192, 0), (30, 20, 5)]
+    inst = _instances(sizes, seed=21)
+    gin = _grads_in(sizes, seed=21)
+    hints, cost = tun.plan_arrays(sizes)
+    assert (cost > 0).all()
+    pb = PackedBatch(sizes, device=DEV, tuning=tun)
+    Qp, qp, Gp, hp, Ap, bp = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
+    out = pb.forward(Qp, qp, Gp, hp, Ap, bp)
+    torch.cuda.synchronize()
+    zs = pb.unpack(out.z, "q")
+    for i, t in enumerate(inst):
+        o = default_options(torch.float32)
+        o.path = 1 if hints[i] == 1 else 0
+        T = [torch.from_numpy(np.float32(x)).unsqueeze(0).to(DEV) for x in t]
+        f = qp_forward(*T, options=o)
+        torch.cuda.synchronize()
+        assert torch.equal(f.z[0], zs[i]), i
