@@ -36,6 +36,9 @@ namespace qpk {
 
 constexpr int NTHREADS = 512;
 constexpr int NWARPS = NTHREADS / 32;
+// Shared-memory budget (bytes) under which the global-memory path keeps its Cholesky panels
+// in shared memory; below every supported device's opt-in limit of the target (227 KB).
+constexpr size_t LARGE_PANEL_SMEM_CAP = 200 * 1024;
 
 enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3 };
 
@@ -75,7 +78,7 @@ struct WsLayout {
 // Dynamic shared memory of the forward kernel.
 template <typename T>
 struct FwdSmem {
-  int nz, m1, N3, ldS, ldM, NT3, NTp;
+  int nz, m1, N3, ldS, ldM, NT3, NTp, pan_smem;
   size_t oSR, oMb, odM, ocb, cbytes, odbl, osplit, ovec, ored, total;
   // large: S/RE, M/X and diag(M) live in the global workspace, only vectors and a work
   // region stay in shared memory.
@@ -108,8 +111,22 @@ struct FwdSmem {
         c = 8 * (size_t)4 * NTHREADS;   // ≥ (2·16·16 + 16) elements of T as well
       }
       cbytes = align_up(c, 16);
-      o += cbytes;
     }
+    pan_smem = 0;
+    const size_t tail = align_up(8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16) +
+                        align_up(8 * ((size_t)n + p + m), 16) +
+                        align_up(es * (3 * (size_t)m1 + 12 * (size_t)p), 16) +
+                        align_up(8 * 4 * NWARPS, 16);
+    if (large) {
+      // The Cholesky panels (pivot scratch plus two 16-row panels of ld round4(p)) go to the
+      // work region when the whole layout stays within LARGE_PANEL_SMEM_CAP bytes.
+      const size_t pc = align_up((2 * 16 * 16 + 16 + 2 * 16 * (size_t)((p + 3) & ~3)) * es, 16);
+      if (o + (pc > cbytes ? pc : cbytes) + tail <= LARGE_PANEL_SMEM_CAP) {
+        pan_smem = 1;
+        if (pc > cbytes) cbytes = pc;
+      }
+    }
+    o += cbytes;
     odbl = o;  o = align_up(o + 8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
     ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 12 * (size_t)p), 16);
@@ -1375,7 +1392,7 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
       [&](const T* Qb, const T* Ab, const T* Gb) {
         return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, cb);
       },
-      [&](const T* dsh) { return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, cb); });
+      [&](const T* dsh) { return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, L.pan_smem != 0, cb); });
 }
 
 // Fixed-size batch, shared-memory path: one block per instance.

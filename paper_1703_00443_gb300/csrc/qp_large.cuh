@@ -10,6 +10,7 @@
 namespace qpk {
 
 constexpr int LNB = 16;   // pivot block of the global-memory path
+static_assert(LNB == 16, "FwdSmem sizes the shared Cholesky panels for 16-wide blocks");
 
 // Shared-memory scratch of the large routines (elements of T): pivot block, its per-pivot
 // rows, and two flags.
@@ -17,14 +18,14 @@ constexpr int LARGE_SMEM_ELEMS = 2 * LNB * LNB + 16;
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
-// C(i, j) −= Σ_{q<nq} Pa[q·ldp + i] · Pb[q·ldp + j] over the rectangle [i0, i1) × [j0, j1)
+// C(i, j) −= Σ_{q<NQ} Pa[q·ldp + i] · Pb[q·ldp + j] over the rectangle [i0, i1) × [j0, j1)
 // (i0, j0 multiples of 4), in 4×4 register micro-tiles spread over the block's threads.
 // `cref(i, j)` returns a reference to C(i, j); `keep(i, j)` selects the entries to update
 // (a tile is skipped when keep_tile(ti, tj) is false).  Panels are padded so that reading
 // the four rows i..i+3 of a tile at the edge stays inside their allocation.
-template <typename T, typename CR, typename KT, typename KE>
+template <typename T, int NQ, typename CR, typename KT, typename KE>
 __device__ __forceinline__ void tile_rank_update(int i0, int i1, int j0, int j1, const T* Pa,
-                                                 const T* Pb, int ldp, int nq, CR cref,
+                                                 const T* Pb, int ldp, CR cref,
                                                  KT keep_tile, KE keep) {
   const int ti_n = (i1 - i0 + 3) / 4, tj_n = (j1 - j0 + 3) / 4;
   for (int t = threadIdx.x; t < ti_n * tj_n; t += NTHREADS) {
@@ -39,7 +40,8 @@ __device__ __forceinline__ void tile_rank_update(int i0, int i1, int j0, int j1,
         const int i = ib + r, j = jb + q;
         c[r * 4 + q] = (i < i1 && j < j1 && keep(i, j)) ? cref(i, j) : T(0);
       }
-    for (int q = 0; q < nq; ++q) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
       T a[4], b[4];
       ld4(a, Pa + (size_t)q * ldp + ib);
       ld4(b, Pb + (size_t)q * ldp + jb);
@@ -147,12 +149,12 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
     __syncthreads();
     // Phase C: rank-LNB update of every entry outside the pivot rows/columns.
     // (a) z/ν block (full square) and λ-by-(z, ν) block: rows 0..N−1, columns 0..m1−1.
-    tile_rank_update<T>(0, N, 0, m1, panP, panC, ldp, LNB,
+    tile_rank_update<T, LNB>(0, N, 0, m1, panP, panC, ldp,
         [&](int i, int j) -> T& { return SR[(size_t)i * ldS + j]; },
         [&](int ib, int jb) { return !(ib >= k0 && ib < k0 + LNB) && !(jb >= k0 && jb < k0 + LNB); },
         [&](int, int) { return true; });
     // (b) λ-by-λ block, upper triangle with diagonal.
-    tile_rank_update<T>(m1, N, m1, N, panP, panC, ldp, LNB,
+    tile_rank_update<T, LNB>(m1, N, m1, N, panP, panC, ldp,
         [&](int i, int j) -> T& {
           const int a = i - m1, b = j - m1;
           return (a == b) ? dM[a] : Mb[(size_t)a * ldM + b];
@@ -174,21 +176,24 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
 
 // Blocked Cholesky factorisation M + D(dsh) = L Lᵀ in the global work matrix Aw (lower
 // triangle), with X = L⁻¹ built in the lower triangle of Mb (whose strict upper triangle
-// keeps M).  Block K of LNB columns: warp 0 factors the diagonal block in shared memory and
-// inverts its factor (V = L_KK⁻¹); all threads form the panel L_IK = A_IK Vᵀ and the new
-// block row X_KJ ← V X_KJ (both published to `pan`); then A_IJ −= L_IK L_JKᵀ (I ≥ J > K) and
-// X_IJ −= L_IK X_KJ (I > K ≥ J).  Returns false on every thread on a non-positive pivot.
+// keeps M).  Block K of LNB columns: warp 0 factors the diagonal block and inverts its factor
+// in registers (lane r holds row r; pivots and rows are exchanged by shuffles), giving
+// V = L_KK⁻¹; all threads form the panel L_IK = A_IK Vᵀ and the new block row
+// X_KJ ← V X_KJ in shared memory (columns beyond a short last block are zero); then
+// A_IJ −= L_IK L_JKᵀ (I ≥ J > K) and X_IJ −= L_IK X_KJ (I > K ≥ J) in register micro-tiles.
+// The two panels live in `sm` after its LARGE_SMEM_ELEMS scratch elements when `pan_in_sm`
+// (then `sm` holds LARGE_SMEM_ELEMS + 2·LNB·round4(p) elements), else in the global `pan`.
+// Returns false on every thread on a non-positive pivot.
 template <typename T>
 __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, T* Aw, T* pan,
-                                       T* sm) {
+                                       bool pan_in_sm, T* sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ldM = p > 0 ? p : 1;
-  T* sA = sm;                  // diagonal block → L_KK (lower)
-  T* sV = sm + LNB * LNB;      // V = L_KK⁻¹
+  T* sV = sm;                  // V = L_KK⁻¹ (LNB × LNB)
   int* flag = reinterpret_cast<int*>(sm + 2 * LNB * LNB);
   const int ldp = round4(p);
-  T* panL = pan;               // panel, q-major: panL[q·ldp + i]
-  T* panX = pan + (size_t)LNB * ldp;   // new block row of X: panX[r·ldp + j]
+  T* panL = pan_in_sm ? sm + LARGE_SMEM_ELEMS : pan;   // panel, q-major: panL[q·ldp + i]
+  T* panX = panL + (size_t)LNB * ldp;                   // new block row of X: panX[r·ldp + j]
 
   for (int e = tid; e < p * p; e += NTHREADS) {
     const int i = e / p, j = e - i * p;
@@ -199,46 +204,44 @@ __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, 
   __syncthreads();
   for (int k0 = 0; k0 < p; k0 += LNB) {
     const int nb = min(LNB, p - k0);
-    // Phase A (warp 0): unblocked Cholesky of the diagonal block and the inverse factor.
+    // Phase A (warp 0, lanes 0..LNB−1 hold the rows): Cholesky of the diagonal block with
+    // V = L_KK⁻¹ accumulated alongside (rows beyond nb are the identity).
     if (warp == 0) {
-      for (int e = lane; e < LNB * LNB; e += 32) {
-        const int r = e / LNB, c = e % LNB;
-        sA[e] = (r < nb && c <= r) ? Aw[(size_t)(k0 + r) * p + k0 + c] : T(0);
+      const int r = lane;
+      T a[LNB], x[LNB];
+#pragma unroll
+      for (int c = 0; c < LNB; ++c) {
+        a[c] = (r < nb && c <= r) ? Aw[(size_t)(k0 + r) * p + k0 + c] : ((r == c) ? T(1) : T(0));
+        x[c] = (r == c) ? T(1) : T(0);
       }
-      __syncwarp();
       bool good = true;
-      for (int k = 0; k < nb; ++k) {
-        const T d = sA[k * LNB + k];
+#pragma unroll
+      for (int k = 0; k < LNB; ++k) {
+        const T d = __shfl_sync(0xffffffffu, a[k], k);
         good = good && isfinite(d) && d > T(0);
         const T inv = rsqrt(d);
-        __syncwarp();
-        if (lane == 0) sA[k * LNB + k] = d * inv;
-        if (lane > k && lane < nb) sA[lane * LNB + k] *= inv;
-        __syncwarp();
-        for (int e = lane; e < LNB * LNB; e += 32) {
-          const int r = e / LNB, c = e % LNB;
-          if (r < nb && c > k && c <= r) sA[e] = fma(-sA[r * LNB + k], sA[c * LNB + k], sA[e]);
+        const T l = a[k] * inv;            // l_rk (r > k)
+#pragma unroll
+        for (int j = k + 1; j < LNB; ++j) {
+          const T lj = __shfl_sync(0xffffffffu, l, j);
+          if (r > k && j <= r) a[j] = fma(-l, lj, a[j]);
         }
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q <= k; ++q) {
+          const T xk = __shfl_sync(0xffffffffu, x[q], k) * inv;
+          if (r == k) x[q] = xk;
+          else if (r > k) x[q] = fma(-l, xk, x[q]);
+        }
       }
-      // Column c of V by lane c: forward substitution.
-      if (lane < LNB) {
-        const int c = lane;
-        for (int r = 0; r < LNB; ++r) {
-          T v = T(0);
-          if (r >= c && r < nb) {
-            T acc = (r == c) ? T(1) : T(0);
-            for (int q = c; q < r; ++q) acc = fma(-sA[r * LNB + q], sV[q * LNB + c], acc);
-            v = acc / sA[r * LNB + r];
-          }
-          sV[r * LNB + c] = v;
-        }
+      if (r < LNB) {
+#pragma unroll
+        for (int c = 0; c < LNB; ++c) sV[r * LNB + c] = (c <= r) ? x[c] : T(0);
       }
       if (lane == 0) flag[0] = good ? 0 : 1;
     }
     __syncthreads();
     if (flag[0]) return false;
-    // Phase B: panel rows and the new block row of X.
+    // Phase B: panel rows (shared memory) and the new block row of X (shared + global).
     for (int i = k0 + nb + tid; i < p; i += NTHREADS) {
       T a[LNB];
 #pragma unroll
@@ -258,23 +261,22 @@ __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, 
         xo[q] = (q < nb && j <= k0 + q) ? Mb[(size_t)(k0 + q) * ldM + j] : T(0);
 #pragma unroll
       for (int r = 0; r < LNB; ++r) {
-        if (r >= nb) break;
         T acc = T(0);
 #pragma unroll
         for (int q = 0; q < LNB; ++q) acc = fma(sV[r * LNB + q], xo[q], acc);
         panX[(size_t)r * ldp + j] = acc;
-        if (j <= k0 + r) Mb[(size_t)(k0 + r) * ldM + j] = acc;
+        if (r < nb && j <= k0 + r) Mb[(size_t)(k0 + r) * ldM + j] = acc;
       }
     }
     __syncthreads();
     // Phase C: trailing update of Aw and of the rows of X below the block.
     const int t0 = k0 + nb;
     if (t0 < p) {
-      tile_rank_update<T>(t0, p, t0, p, panL, panL, ldp, nb,
+      tile_rank_update<T, LNB>(t0, p, t0, p, panL, panL, ldp,
           [&](int i, int j) -> T& { return Aw[(size_t)i * p + j]; },
           [&](int ib, int jb) { return jb <= ib + 3; },
           [&](int i, int j) { return j <= i; });
-      tile_rank_update<T>(t0, p, 0, t0, panL, panX, ldp, nb,
+      tile_rank_update<T, LNB>(t0, p, 0, t0, panL, panX, ldp,
           [&](int i, int j) -> T& { return Mb[(size_t)i * ldM + j]; },
           [&](int, int) { return true; },
           [&](int, int) { return true; });
