@@ -39,6 +39,12 @@ constexpr int NWARPS = NTHREADS / 32;
 // Shared-memory budget (bytes) under which the global-memory path keeps its Cholesky panels
 // in shared memory; below every supported device's opt-in limit of the target (227 KB).
 constexpr size_t LARGE_PANEL_SMEM_CAP = 200 * 1024;
+// Column block of the global-memory Cholesky: 32 for FP32, 16 for FP64 (one warp holds the
+// pivot block's row and its inverse's row in registers).
+__host__ __device__ constexpr int chol_nb(int esz) { return esz == 4 ? 32 : 16; }
+// Largest p for which the global-memory path factors with the register-tile Cholesky
+// (4×4 tiles of the lower triangle in at most two register slots per thread).
+constexpr int REG_CHOL_MAX_P = 176;
 
 enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3 };
 
@@ -54,7 +60,8 @@ __host__ __device__ inline int padded_nz(int n, int m) { return n + ((4 - (n + m
 // Layout shared by both kernel paths (the backward pass reads only this prefix):
 // SR = [S; RE] ((m1+p) × m1, m1 = nz + neq), the p×p block with X = L⁻¹ (lower) and M
 // (strict upper), the FP64 iterate (z, s, λ, ν) and the status word.  The global-memory
-// path appends diag(M), its Cholesky work matrix and its panel scratch.
+// path appends diag(M), its Cholesky work matrix (row stride round4(p)) and its panel
+// scratch (the sweep's two 16-row panels, or the Cholesky's panel and staging buffer).
 struct WsLayout {
   size_t oSR, oX, oIt, oSt, odM, oAw, oPan, inst;
   __host__ __device__ void init(int n, int nz, int p, int m, int esz, bool large) {
@@ -66,10 +73,12 @@ struct WsLayout {
     size_t o = align_up(oSt + 16, 256);
     odM = oAw = oPan = o;
     if (large) {
-      const size_t N = m1 + p, ldp = (N + 3) / 4 * 4;
+      const size_t N = m1 + p, ldp = (N + 7) / 8 * 8;
       odM = o;  o = align_up(o + (size_t)p * esz, 256);
-      oAw = o;  o = align_up(o + (size_t)p * p * esz, 256);
-      oPan = o; o = align_up(o + 2 * 16 * ldp * esz, 256);
+      const size_t cpan = 2 * (size_t)chol_nb(esz) * (size_t)((p + 7) & ~7);
+      const size_t span = 2 * 16 * ldp;
+      oAw = o;  o = align_up(o + (size_t)p * ((p + 3) & ~3) * esz, 256);
+      oPan = o; o = align_up(o + (span > cpan ? span : cpan) * esz, 256);
     }
     inst = o;
   }
@@ -78,7 +87,7 @@ struct WsLayout {
 // Dynamic shared memory of the forward kernel.
 template <typename T>
 struct FwdSmem {
-  int nz, m1, N3, ldS, ldM, NT3, NTp, pan_smem;
+  int nz, m1, N3, ldS, ldM, NT3, NTp, pan_smem, span_smem;
   size_t oSR, oMb, odM, ocb, cbytes, odbl, osplit, ovec, ored, total;
   // large: S/RE, M/X and diag(M) live in the global workspace, only vectors and a work
   // region stay in shared memory.
@@ -108,22 +117,36 @@ struct FwdSmem {
         c = (a > b ? a : b) * es + 64;
         if (c < 8 * (size_t)NTHREADS) c = 8 * (size_t)NTHREADS;
       } else {
-        c = 8 * (size_t)4 * NTHREADS;   // ≥ (2·16·16 + 16) elements of T as well
+        // ≥ the pivot scratch of the large routines, and ≥ the panels of the register-tile
+        // Cholesky, which the global-memory path uses while p ≤ REG_CHOL_MAX_P.
+        c = 8 * (size_t)4 * NTHREADS;
+        const size_t nt = (size_t)((p < REG_CHOL_MAX_P ? p : REG_CHOL_MAX_P) + 3) / 4;
+        const size_t rc = (2 * (32 * nt + 16) + 16) * es;
+        if (rc > c) c = rc;
       }
       cbytes = align_up(c, 16);
     }
-    pan_smem = 0;
+    pan_smem = span_smem = 0;
     const size_t tail = align_up(8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16) +
                         align_up(8 * ((size_t)n + p + m), 16) +
                         align_up(es * (3 * (size_t)m1 + 12 * (size_t)p), 16) +
                         align_up(8 * 4 * NWARPS, 16);
     if (large) {
-      // The Cholesky panels (pivot scratch plus two 16-row panels of ld round4(p)) go to the
-      // work region when the whole layout stays within LARGE_PANEL_SMEM_CAP bytes.
-      const size_t pc = align_up((2 * 16 * 16 + 16 + 2 * 16 * (size_t)((p + 3) & ~3)) * es, 16);
+      // The Cholesky panel and staging buffer (pivot scratch plus 2·chol_nb rows of ld
+      // round8(p)) go to the work region when the whole layout stays within
+      // LARGE_PANEL_SMEM_CAP bytes.
+      // The setup sweep's two 16-row panels (ld round8(m1 + p)) likewise, after its pivot
+      // scratch, if they fit too.
+      const size_t nb = (size_t)chol_nb((int)es);
+      const size_t pc = align_up((nb * nb + 16 + 2 * nb * (size_t)((p + 7) & ~7)) * es, 16);
+      const size_t sc = align_up((2 * 16 * 16 + 16 + 2 * 16 * (size_t)((N3 + 7) & ~7)) * es, 16);
       if (o + (pc > cbytes ? pc : cbytes) + tail <= LARGE_PANEL_SMEM_CAP) {
         pan_smem = 1;
         if (pc > cbytes) cbytes = pc;
+      }
+      if (o + (sc > cbytes ? sc : cbytes) + tail <= LARGE_PANEL_SMEM_CAP) {
+        span_smem = 1;
+        if (sc > cbytes) cbytes = sc;
       }
     }
     o += cbytes;
@@ -1390,9 +1413,18 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
   fwd_body<T>(I, L, sm, SR, Mb, dM, true,
       [&](const T* Qb, const T* Ab, const T* Gb) {
-        return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, cb);
+        return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, L.span_smem != 0, cb);
       },
-      [&](const T* dsh) { return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, L.pan_smem != 0, cb); });
+      [&](const T* dsh) {
+        // Small Schur complements: the register-tile routine (M read from and X written to
+        // the workspace, panels in shared memory); otherwise the blocked global routine.
+        const int NT = (p + 3) >> 2, nt = NT * (NT + 1) / 2, ldM = p > 0 ? p : 1;
+        if (nt <= NTHREADS) return chol_inv<T, 1>(p, Mb, ldM, dM, dsh, cb);
+        if constexpr (sizeof(T) == 4) {
+          if (nt <= 2 * NTHREADS && p <= REG_CHOL_MAX_P) return chol_inv<T, 2>(p, Mb, ldM, dM, dsh, cb);
+        }
+        return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, L.pan_smem != 0, cb);
+      });
 }
 
 // Fixed-size batch, shared-memory path: one block per instance.

@@ -2,15 +2,15 @@
 // of an instance do not fit in shared memory.  Same method and same results layout as the
 // register-tile routines in qp_device.cuh (S and RE in SR, M in the strict upper triangle of
 // Mb plus dM, X = L⁻¹ in the lower triangle of Mb), but the matrices live in the instance's
-// global workspace (L2-resident during the solve) and pivots are taken in blocks of LNB: one
-// warp handles the pivot block in shared memory, all threads then transform the panel and
-// apply the rank-LNB update, with three barriers per pivot block.
+// global workspace (L2-resident during the solve).  Pivots are taken in blocks: one warp
+// handles the pivot block, all threads then form the panel and apply the rank-block update
+// to the trailing matrix (LNB = 16 columns per block in the setup sweep, chol_nb columns in
+// the per-iteration Cholesky, whose current block column and panel stay in shared memory).
 #pragma once
 
 namespace qpk {
 
 constexpr int LNB = 16;   // pivot block of the global-memory path
-static_assert(LNB == 16, "FwdSmem sizes the shared Cholesky panels for 16-wide blocks");
 
 // Shared-memory scratch of the large routines (elements of T): pivot block, its per-pivot
 // rows, and two flags.
@@ -18,70 +18,31 @@ constexpr int LARGE_SMEM_ELEMS = 2 * LNB * LNB + 16;
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
-// C(i, j) −= Σ_{q<NQ} Pa[q·ldp + i] · Pb[q·ldp + j] over the rectangle [i0, i1) × [j0, j1)
-// (i0, j0 multiples of 4), in 4×4 register micro-tiles spread over the block's threads.
-// `cref(i, j)` returns a reference to C(i, j); `keep(i, j)` selects the entries to update
-// (a tile is skipped when keep_tile(ti, tj) is false).  Panels are padded so that reading
-// the four rows i..i+3 of a tile at the edge stays inside their allocation.
-template <typename T, int NQ, typename CR, typename KT, typename KE>
-__device__ __forceinline__ void tile_rank_update(int i0, int i1, int j0, int j1, const T* Pa,
-                                                 const T* Pb, int ldp, CR cref,
-                                                 KT keep_tile, KE keep) {
-  const int ti_n = (i1 - i0 + 3) / 4, tj_n = (j1 - j0 + 3) / 4;
-  for (int t = threadIdx.x; t < ti_n * tj_n; t += NTHREADS) {
-    const int ti = t / tj_n, tj = t - ti * tj_n;
-    const int ib = i0 + 4 * ti, jb = j0 + 4 * tj;
-    if (!keep_tile(ib, jb)) continue;
-    T c[16];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = ib + r, j = jb + q;
-        c[r * 4 + q] = (i < i1 && j < j1 && keep(i, j)) ? cref(i, j) : T(0);
-      }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T a[4], b[4];
-      ld4(a, Pa + (size_t)q * ldp + ib);
-      ld4(b, Pb + (size_t)q * ldp + jb);
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) c[r * 4 + cc] = fma(-a[r], b[cc], c[r * 4 + cc]);
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = ib + r, j = jb + q;
-        if (i < i1 && j < j1 && keep(i, j)) cref(i, j) = c[r * 4 + q];
-      }
-  }
-}
-
 // Blocked symmetric Gauss-Jordan sweep over the first m1 pivots (m1 = nz + neq, a multiple of
 // LNB) of [[Q̃, Aᵀ, Gᵀ], [A, 0, 0], [G, 0, 0]] held in global memory:
 //   rows 0..m1−1 of SR (full square, both triangles) = the z/ν block,
 //   rows m1.. of SR (nineq × m1)                     = the λ-by-(z, ν) block,
 //   strict upper triangle of Mb plus dM               = the λ-by-λ block.
 // Each pivot block replays the scalar sweeps of its LNB pivots on every panel row (the
-// pivot columns of a row), publishes ĉ and ĉ·D⁻¹ to `pan` (q-major, ld = N), and every
-// other entry takes the accumulated update a_ij −= Σ_q (ĉ_iq/d_q) ĉ_jq.  Afterwards the
-// blocks are negated where the swept matrix holds −S and −M, so SR = [S; RE] and Mb/dM
-// hold M exactly as the register-tile sweep leaves them.
+// pivot columns of a row, read and written as 16-byte vectors), publishes ĉ and ĉ·D⁻¹ to
+// the panels (q-major, ld = round8(N); in shared memory after the pivot scratch when
+// `pan_in_sm`, else in the global `pan`), and every other entry takes the accumulated update
+// a_ij −= Σ_q (ĉ_iq/d_q) ĉ_jq in 8×4 register micro-tiles.  Afterwards the blocks are
+// negated where the swept matrix holds −S and −M, so SR = [S; RE] and Mb/dM hold M exactly
+// as the register-tile sweep leaves them.
 template <typename T>
 __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* __restrict__ Q,
                                           const T* __restrict__ A, const T* __restrict__ G,
-                                          T* SR, T* Mb, T* dM, T* pan, T* sm) {
+                                          T* SR, T* Mb, T* dM, T* pan, bool pan_in_sm, T* sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m1 = nz + m, N = m1 + p, ldS = m1, ldM = p > 0 ? p : 1;
+  const bool mvec = (p & 3) == 0;   // rows of Mb 16-byte aligned
   T* sB = sm;                  // pivot block (LNB × LNB), swept in place
   T* sR = sm + LNB * LNB;      // r_k rows
   int* flag = reinterpret_cast<int*>(sm + 2 * LNB * LNB);
-  const int ldp = round4(N);
-  T* panC = pan;               // ĉ, q-major: panC[q·ldp + i]
-  T* panP = pan + (size_t)LNB * ldp;
+  const int ldp = (N + 7) & ~7;
+  T* panC = pan_in_sm ? sm + LARGE_SMEM_ELEMS : pan;   // ĉ, q-major: panC[q·ldp + i]
+  T* panP = panC + (size_t)LNB * ldp;                  // ĉ·D⁻¹
 
   for (int e = tid; e < (m1 + p) * m1; e += NTHREADS) {
     const int i = e / m1, j = e - i * m1;
@@ -91,6 +52,8 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
   for (int e = tid; e < p; e += NTHREADS) dM[e] = T(0);
   __syncthreads();
 
+  const int RT = (N + 7) >> 3, CT = m1 >> 2;           // tiles of the SR region
+  const int RTp = (p + 7) >> 3, CTp = (p + 3) >> 2;    // tile rows / columns of the λλ block
   for (int k0 = 0; k0 < m1; k0 += LNB) {
     // Phase A (warp 0): scalar sweeps of the pivot block, recording r_k.
     if (warp == 0) {
@@ -127,9 +90,14 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
     // Phase B: replay the sweeps on every panel row.
     for (int i = tid; i < N; i += NTHREADS) {
       if (i >= k0 && i < k0 + LNB) continue;
+      T* row = SR + (size_t)i * ldS + k0;
       T v[LNB];
 #pragma unroll
-      for (int q = 0; q < LNB; ++q) v[q] = (i < m1) ? SR[(size_t)i * ldS + k0 + q] : SR[(size_t)i * ldS + k0 + q];
+      for (int q = 0; q < LNB; q += 4) {
+        T t4[4];
+        ld4(t4, row + q);
+        v[q] = t4[0]; v[q + 1] = t4[1]; v[q + 2] = t4[2]; v[q + 3] = t4[3];
+      }
 #pragma unroll
       for (int k = 0; k < LNB; ++k) {
         const T c = v[k];
@@ -141,26 +109,104 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
         v[k] = c * sR[k * LNB + k];
       }
 #pragma unroll
-      for (int q = 0; q < LNB; ++q) {
-        SR[(size_t)i * ldS + k0 + q] = v[q];
-        if (i < m1) SR[(size_t)(k0 + q) * ldS + i] = v[q];
+      for (int q = 0; q < LNB; q += 4) st4(row + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+      if (i < m1) {
+#pragma unroll
+        for (int q = 0; q < LNB; ++q) SR[(size_t)(k0 + q) * ldS + i] = v[q];
       }
     }
     __syncthreads();
-    // Phase C: rank-LNB update of every entry outside the pivot rows/columns.
+    // Phase C: rank-LNB update of every entry outside the pivot rows/columns, 8×4 tiles.
     // (a) z/ν block (full square) and λ-by-(z, ν) block: rows 0..N−1, columns 0..m1−1.
-    tile_rank_update<T, LNB>(0, N, 0, m1, panP, panC, ldp,
-        [&](int i, int j) -> T& { return SR[(size_t)i * ldS + j]; },
-        [&](int ib, int jb) { return !(ib >= k0 && ib < k0 + LNB) && !(jb >= k0 && jb < k0 + LNB); },
-        [&](int, int) { return true; });
-    // (b) λ-by-λ block, upper triangle with diagonal.
-    tile_rank_update<T, LNB>(m1, N, m1, N, panP, panC, ldp,
-        [&](int i, int j) -> T& {
-          const int a = i - m1, b = j - m1;
-          return (a == b) ? dM[a] : Mb[(size_t)a * ldM + b];
-        },
-        [&](int ib, int jb) { return jb + 3 >= ib; },
-        [&](int i, int j) { return j >= i; });
+    for (int t = tid; t < RT * CT; t += NTHREADS) {
+      const int R = t / CT, ib = 8 * R, jb = 4 * (t - R * CT);
+      if ((ib >= k0 && ib < k0 + LNB) || (jb >= k0 && jb < k0 + LNB)) continue;
+      T c[32];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        T t4[4] = {T(0), T(0), T(0), T(0)};
+        if (ib + rr < N) ld4(t4, SR + (size_t)(ib + rr) * ldS + jb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[rr * 4 + q] = t4[q];
+      }
+#pragma unroll 4
+      for (int q = 0; q < LNB; ++q) {
+        T a0[4], a1[4], b[4];
+        ld4(a0, panP + (size_t)q * ldp + ib);
+        ld4(a1, panP + (size_t)q * ldp + ib + 4);
+        ld4(b, panC + (size_t)q * ldp + jb);
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            c[rr * 4 + cc] = fma(-a0[rr], b[cc], c[rr * 4 + cc]);
+            c[(rr + 4) * 4 + cc] = fma(-a1[rr], b[cc], c[(rr + 4) * 4 + cc]);
+          }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr)
+        if (ib + rr < N)
+          st4(SR + (size_t)(ib + rr) * ldS + jb, c[rr * 4], c[rr * 4 + 1], c[rr * 4 + 2], c[rr * 4 + 3]);
+    }
+    // (b) λ-by-λ block, upper triangle with diagonal: tile row R (rows 8R..8R+7) holds the
+    // CTp − 2R tiles of columns 8R..p−1; F(R) = R·(CTp + 1 − R) tiles precede it.
+    const int ntp = RTp * (CTp + 1 - RTp);
+    for (int t = tid; t < ntp; t += NTHREADS) {
+      int lo = 0, hi = RTp - 1;
+      while (lo < hi) {   // largest R with F(R) ≤ t
+        const int mid = (lo + hi + 1) >> 1;
+        if (mid * (CTp + 1 - mid) <= t) lo = mid; else hi = mid - 1;
+      }
+      const int R = lo, ia = 8 * R, jb = 4 * (2 * R + (t - R * (CTp + 1 - R)));
+      T c[32];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const int a = ia + rr;
+        if (mvec && a < p && jb > a) {
+          T t4[4];
+          ld4(t4, Mb + (size_t)a * ldM + jb);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) c[rr * 4 + q] = t4[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int b = jb + q;
+            c[rr * 4 + q] = (a < p && b < p && b >= a) ? ((a == b) ? dM[a] : Mb[(size_t)a * ldM + b])
+                                                      : T(0);
+          }
+        }
+      }
+#pragma unroll 4
+      for (int q = 0; q < LNB; ++q) {
+        T a0[4], a1[4], b[4];
+        ld4(a0, panP + (size_t)q * ldp + m1 + ia);
+        ld4(a1, panP + (size_t)q * ldp + m1 + ia + 4);
+        ld4(b, panC + (size_t)q * ldp + m1 + jb);
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            c[rr * 4 + cc] = fma(-a0[rr], b[cc], c[rr * 4 + cc]);
+            c[(rr + 4) * 4 + cc] = fma(-a1[rr], b[cc], c[(rr + 4) * 4 + cc]);
+          }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const int a = ia + rr;
+        if (mvec && a < p && jb > a) {
+          st4(Mb + (size_t)a * ldM + jb, c[rr * 4], c[rr * 4 + 1], c[rr * 4 + 2], c[rr * 4 + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int b = jb + q;
+            if (a < p && b < p && b >= a) {
+              if (a == b) dM[a] = c[rr * 4 + q];
+              else Mb[(size_t)a * ldM + b] = c[rr * 4 + q];
+            }
+          }
+        }
+      }
+    }
     __syncthreads();
   }
   // Negate the z/ν block (it holds −S) and the λ-by-λ block (it holds −M).
@@ -174,112 +220,200 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
   return true;
 }
 
-// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ in the global work matrix Aw (lower
-// triangle), with X = L⁻¹ built in the lower triangle of Mb (whose strict upper triangle
-// keeps M).  Block K of LNB columns: warp 0 factors the diagonal block and inverts its factor
-// in registers (lane r holds row r; pivots and rows are exchanged by shuffles), giving
-// V = L_KK⁻¹; all threads form the panel L_IK = A_IK Vᵀ and the new block row
-// X_KJ ← V X_KJ in shared memory (columns beyond a short last block are zero); then
-// A_IJ −= L_IK L_JKᵀ (I ≥ J > K) and X_IJ −= L_IK X_KJ (I > K ≥ J) in register micro-tiles.
-// The two panels live in `sm` after its LARGE_SMEM_ELEMS scratch elements when `pan_in_sm`
-// (then `sm` holds LARGE_SMEM_ELEMS + 2·LNB·round4(p) elements), else in the global `pan`.
-// Returns false on every thread on a non-positive pivot.
+// Pivot block of the global-memory Cholesky, in registers of warp 0 (lane r holds row r of
+// the block): L_KK from the block column staged in Sb (Sb[c·ldp + i] = A(i, k0 + c)), and
+// V = L_KK⁻¹ written to sV (row-major NB × NB).  Rows beyond nb are the identity.  Each
+// column step shifts the row left by one, so the pivot column is always a[0] and the loop
+// needs no unrolling; pivots and rows travel by shuffles.  flag[0] = 1 on a non-positive or
+// non-finite pivot.
+template <typename T, int NB>
+__device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int ldp, T* sV,
+                                               int* flag) {
+  static_assert(NB <= 32, "one lane per row");
+  const int r = threadIdx.x & 31;
+  T a[NB], x[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    a[c] = (r < nb && c <= r) ? Sb[(size_t)c * ldp + k0 + r] : ((r == c) ? T(1) : T(0));
+    x[c] = (r == c) ? T(1) : T(0);
+  }
+  bool good = true;
+#pragma unroll 1
+  for (int k = 0; k < NB; ++k) {
+    const T d = __shfl_sync(0xffffffffu, a[0], k);
+    good = good && isfinite(d) && d > T(0);
+    const T inv = rsqrt(d);
+    const T l = (r > k) ? a[0] * inv : T(0);   // l_rk below the pivot
+#pragma unroll
+    for (int jj = 1; jj < NB; ++jj) {
+      const T lj = __shfl_sync(0xffffffffu, l, (k + jj) & 31);
+      if (k + jj <= r) a[jj] = fma(-l, lj, a[jj]);
+    }
+#pragma unroll
+    for (int jj = 0; jj + 1 < NB; ++jj) a[jj] = a[jj + 1];
+    a[NB - 1] = T(0);
+    // Row k of V is final once divided by l_kk; the rows below eliminate it.
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const T xk = __shfl_sync(0xffffffffu, x[q], k) * inv;
+      x[q] = (r == k) ? xk : fma(-l, xk, x[q]);
+    }
+  }
+  if (r < NB) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) sV[r * NB + c] = x[c];
+  }
+  if (r == 0) flag[0] = good ? 0 : 1;
+}
+
+// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ, with X = L⁻¹ built in the lower triangle
+// of Mb (whose strict upper triangle keeps M).  The trailing matrix lives in the global work
+// matrix Aw (lower triangle, row stride round4(p)); the current block column, the panel and
+// the pivot inverse live in shared memory (or, for very large p, in the global `pan`).
+// Block K = columns [k0, k0 + NB), t0 = k0 + NB, with block column K staged in S:
+//   A: warp 0 factors the diagonal block from S and inverts its factor, V = L_KK⁻¹;
+//   B: the panel P (NB rows of ld round8(p)) receives, by column range,
+//        P[c][j] = (V X_K·)[c][j]  for j < t0   (new block row of X),
+//        P[c][i] = (A_IK Vᵀ)[i][c] for i ≥ t0  (the panel L_IK, A_IK read from S);
+//   C: the new block row of X is copied from P to Mb (after B, whose items read the old
+//      one), and every lower-triangle entry (i ≥ t0, j ≤ i) takes
+//      C(i, j) −= Σ_c P[c][i] P[c][j], which is A_IJ −= L_IK L_JKᵀ for j ≥ t0 and
+//      X_IJ −= L_IK X_KJ for j < t0, over the tiles of that region only, in 8×4 register
+//      micro-tiles (tile row R, rows 8R..8R+7, holds the 2R + 2 tiles of columns 0..8R+7).
+//      Tiles of block column K + 1 go to S instead of Aw: they are final and only the next
+//      pivot block and panel read them.
+// NB is 32 for FP32 and 16 for FP64 (register room of the pivot block).  Returns false on
+// every thread on a non-positive pivot.
 template <typename T>
 __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, T* Aw, T* pan,
                                        bool pan_in_sm, T* sm) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ldM = p > 0 ? p : 1;
-  T* sV = sm;                  // V = L_KK⁻¹ (LNB × LNB)
-  int* flag = reinterpret_cast<int*>(sm + 2 * LNB * LNB);
-  const int ldp = round4(p);
-  T* panL = pan_in_sm ? sm + LARGE_SMEM_ELEMS : pan;   // panel, q-major: panL[q·ldp + i]
-  T* panX = panL + (size_t)LNB * ldp;                   // new block row of X: panX[r·ldp + j]
+  constexpr int NB = chol_nb((int)sizeof(T));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ldM = p > 0 ? p : 1, ldA = round4(p), ldp = (p + 7) & ~7;
+  const bool xvec = (p & 3) == 0;                   // rows of Mb 16-byte aligned
+  T* sV = sm;                                       // V (NB × NB)
+  int* flag = reinterpret_cast<int*>(sm + NB * NB);
+  T* P = pan_in_sm ? sm + NB * NB + 16 : pan;       // panel: P[c·ldp + j]
+  T* S = P + (size_t)NB * ldp;                      // block column: S[c·ldp + i] = A(i, k0 + c)
 
   for (int e = tid; e < p * p; e += NTHREADS) {
     const int i = e / p, j = e - i * p;
     if (j > i) continue;
-    Aw[e] = (i == j) ? dM[i] + dsh[i] : Mb[(size_t)j * ldM + i];
+    const T v = (i == j) ? dM[i] + dsh[i] : Mb[(size_t)j * ldM + i];
+    if (j < NB) S[(size_t)j * ldp + i] = v;
+    else Aw[(size_t)i * ldA + j] = v;
     Mb[e] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
-  for (int k0 = 0; k0 < p; k0 += LNB) {
-    const int nb = min(LNB, p - k0);
-    // Phase A (warp 0, lanes 0..LNB−1 hold the rows): Cholesky of the diagonal block with
-    // V = L_KK⁻¹ accumulated alongside (rows beyond nb are the identity).
-    if (warp == 0) {
-      const int r = lane;
-      T a[LNB], x[LNB];
-#pragma unroll
-      for (int c = 0; c < LNB; ++c) {
-        a[c] = (r < nb && c <= r) ? Aw[(size_t)(k0 + r) * p + k0 + c] : ((r == c) ? T(1) : T(0));
-        x[c] = (r == c) ? T(1) : T(0);
-      }
-      bool good = true;
-#pragma unroll
-      for (int k = 0; k < LNB; ++k) {
-        const T d = __shfl_sync(0xffffffffu, a[k], k);
-        good = good && isfinite(d) && d > T(0);
-        const T inv = rsqrt(d);
-        const T l = a[k] * inv;            // l_rk (r > k)
-#pragma unroll
-        for (int j = k + 1; j < LNB; ++j) {
-          const T lj = __shfl_sync(0xffffffffu, l, j);
-          if (r > k && j <= r) a[j] = fma(-l, lj, a[j]);
-        }
-#pragma unroll
-        for (int q = 0; q <= k; ++q) {
-          const T xk = __shfl_sync(0xffffffffu, x[q], k) * inv;
-          if (r == k) x[q] = xk;
-          else if (r > k) x[q] = fma(-l, xk, x[q]);
-        }
-      }
-      if (r < LNB) {
-#pragma unroll
-        for (int c = 0; c < LNB; ++c) sV[r * LNB + c] = (c <= r) ? x[c] : T(0);
-      }
-      if (lane == 0) flag[0] = good ? 0 : 1;
-    }
+  for (int k0 = 0; k0 < p; k0 += NB) {
+    const int nb = min(NB, p - k0), t0 = k0 + nb;
+    if (warp == 0) gchol_pivot_block<T, NB>(k0, nb, S, ldp, sV, flag);
     __syncthreads();
     if (flag[0]) return false;
-    // Phase B: panel rows (shared memory) and the new block row of X (shared + global).
-    for (int i = k0 + nb + tid; i < p; i += NTHREADS) {
-      T a[LNB];
+    // Phase B: work item (g, j) forms outputs c = 8g..8g+7 of panel column j (the X block row
+    // for j < t0, the L panel for j ≥ t0); j runs fastest so V is read by broadcast.
+    for (int w = tid; w < p * (NB / 8); w += NTHREADS) {
+      const int g = w / p, j = w - g * p;
+      T v[NB];
+      if (j < t0) {
 #pragma unroll
-      for (int q = 0; q < LNB; ++q) a[q] = (q < nb) ? Aw[(size_t)i * p + k0 + q] : T(0);
+        for (int q = 0; q < NB; ++q)
+          v[q] = (q < nb && j <= k0 + q) ? Mb[(size_t)(k0 + q) * ldM + j] : T(0);
+      } else {
 #pragma unroll
-      for (int c = 0; c < LNB; ++c) {
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < LNB; ++q) acc = fma(a[q], sV[c * LNB + q], acc);
-        panL[(size_t)c * ldp + i] = acc;
+        for (int q = 0; q < NB; ++q) v[q] = (q < nb) ? S[(size_t)q * ldp + j] : T(0);
       }
-    }
-    for (int j = tid; j < k0 + nb; j += NTHREADS) {
-      T xo[LNB];
+      // X row: P[c][j] = Σ_q V[c][q] X[k0+q][j];  L panel: P[c][j] = Σ_q A[j][k0+q] V[c][q].
+      T acc[8];
 #pragma unroll
-      for (int q = 0; q < LNB; ++q)
-        xo[q] = (q < nb && j <= k0 + q) ? Mb[(size_t)(k0 + q) * ldM + j] : T(0);
+      for (int e = 0; e < 8; ++e) acc[e] = T(0);
 #pragma unroll
-      for (int r = 0; r < LNB; ++r) {
-        T acc = T(0);
+      for (int q = 0; q < NB; q += 4) {
 #pragma unroll
-        for (int q = 0; q < LNB; ++q) acc = fma(sV[r * LNB + q], xo[q], acc);
-        panX[(size_t)r * ldp + j] = acc;
-        if (r < nb && j <= k0 + r) Mb[(size_t)(k0 + r) * ldM + j] = acc;
+        for (int e = 0; e < 8; ++e) {
+          T wv[4];
+          ld4(wv, sV + (8 * g + e) * NB + q);
+          acc[e] = fma(wv[0], v[q], acc[e]);
+          acc[e] = fma(wv[1], v[q + 1], acc[e]);
+          acc[e] = fma(wv[2], v[q + 2], acc[e]);
+          acc[e] = fma(wv[3], v[q + 3], acc[e]);
+        }
       }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) P[(size_t)(8 * g + e) * ldp + j] = acc[e];
     }
     __syncthreads();
-    // Phase C: trailing update of Aw and of the rows of X below the block.
-    const int t0 = k0 + nb;
+    for (int e = tid; e < nb * t0; e += NTHREADS) {
+      const int c = e / t0, j = e - c * t0;
+      if (j <= k0 + c) Mb[(size_t)(k0 + c) * ldM + j] = P[(size_t)c * ldp + j];
+    }
+    // Phase C: lower-triangle 8×4 tiles of rows [t0, p) (t0 is a multiple of 8).
     if (t0 < p) {
-      tile_rank_update<T, LNB>(t0, p, t0, p, panL, panL, ldp,
-          [&](int i, int j) -> T& { return Aw[(size_t)i * p + j]; },
-          [&](int ib, int jb) { return jb <= ib + 3; },
-          [&](int i, int j) { return j <= i; });
-      tile_rank_update<T, LNB>(t0, p, 0, t0, panL, panX, ldp,
-          [&](int i, int j) -> T& { return Mb[(size_t)i * ldM + j]; },
-          [&](int, int) { return true; },
-          [&](int, int) { return true; });
+      const int R0 = t0 >> 3, R1 = (p + 7) >> 3, t1 = t0 + NB;
+      const long long base = (long long)R0 * (R0 + 1);
+      const long long ntile = (long long)R1 * (R1 + 1) - base;
+      for (long long t = tid; t < ntile; t += NTHREADS) {
+        const long long u = t + base;   // tiles before tile row R: R(R + 1)
+        int R = (int)((sqrtf(4.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+        while ((long long)(R + 1) * (R + 2) <= u) ++R;
+        while ((long long)R * (R + 1) > u) --R;
+        const int ib = 8 * R, jb = 4 * (int)(u - (long long)R * (R + 1));
+        const bool isx = jb < t0, stage = !isx && jb < t1;
+        T* Cb = isx ? Mb : Aw;
+        const int ldc = isx ? ldM : ldA;
+        const bool vec = isx ? xvec : true;
+        T c[32];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+          const int i = ib + rr;
+          if (vec && i < p && jb + 3 <= i) {
+            T t4[4];
+            ld4(t4, Cb + (size_t)i * ldc + jb);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[rr * 4 + q] = t4[q];
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              c[rr * 4 + q] = (i < p && jb + q <= i) ? Cb[(size_t)i * ldc + jb + q] : T(0);
+          }
+        }
+#pragma unroll 4
+        for (int q = 0; q < NB; ++q) {
+          T a0[4], a1[4], b[4];
+          ld4(a0, P + (size_t)q * ldp + ib);
+          ld4(a1, P + (size_t)q * ldp + ib + 4);
+          ld4(b, P + (size_t)q * ldp + jb);
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              c[rr * 4 + cc] = fma(-a0[rr], b[cc], c[rr * 4 + cc]);
+              c[(rr + 4) * 4 + cc] = fma(-a1[rr], b[cc], c[(rr + 4) * 4 + cc]);
+            }
+        }
+        if (stage) {
+          // Block column K + 1: S[(jb − t0 + q)·ldp + i].
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) {
+            const int i = ib + rr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (i < p && jb + q <= i) S[(size_t)(jb - t0 + q) * ldp + i] = c[rr * 4 + q];
+          }
+        } else {
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) {
+            const int i = ib + rr;
+            if (vec && i < p && jb + 3 <= i) {
+              st4(Cb + (size_t)i * ldc + jb, c[rr * 4], c[rr * 4 + 1], c[rr * 4 + 2], c[rr * 4 + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (i < p && jb + q <= i) Cb[(size_t)i * ldc + jb + q] = c[rr * 4 + q];
+            }
+          }
+        }
+      }
     }
     __syncthreads();
   }
