@@ -45,6 +45,13 @@ __host__ __device__ constexpr int chol_nb(int esz) { return esz == 4 ? 32 : 16; 
 // Largest p for which the global-memory path factors with the register-tile Cholesky
 // (4×4 tiles of the lower triangle in at most two register slots per thread).
 constexpr int REG_CHOL_MAX_P = 176;
+// Whether the global-memory path factors a p×p Schur complement with the register-tile
+// Cholesky (X = L⁻¹ in Mb, solves by two products) rather than the blocked routine (blocked L
+// with inverted diagonal blocks in Mb, solves by block substitution).
+__host__ __device__ inline bool reg_chol_ok(int p, int esz) {
+  const int NT = (p + 3) >> 2, nt = NT * (NT + 1) / 2;
+  return nt <= NTHREADS || (esz == 4 && nt <= 2 * NTHREADS && p <= REG_CHOL_MAX_P);
+}
 
 enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3 };
 
@@ -1086,10 +1093,10 @@ namespace qpk {
 // global memory; setup() fills them (the setup sweep) and factor(dsh) factors
 // M + D(dsh) into X.  With ws_resident the factors already live in the workspace, otherwise
 // they are copied there for the backward pass.
-template <typename T, typename FS, typename FF>
+template <typename T, typename FS, typename FF, typename FV>
 __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& L,
                                          unsigned char* sm, T* SR, T* Mb, T* dM,
-                                         bool ws_resident, FS setup, FF factor) {
+                                         bool ws_resident, FS setup, FF factor, FV solve) {
   using V = typename Split<T>::V;
   const int tid = threadIdx.x;
   const int n = P.n, p = P.p, m = P.m;
@@ -1191,7 +1198,7 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
       __syncthreads();
       for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] - hb[i];
       __syncthreads();
-      chol_solve(p, Mb, ldM, rhs, y, dl, tscr);
+      solve(rhs, y, dl, tscr);
       mv_cols(SR + (size_t)m1 * ldS, ldS, p, m1, TRI_ALL, dl, tscr,
               [&](int c, T val) { dzn[c] = wv[c] - val; });
       float v[4] = {-INFINITY, 0.f, -INFINITY, 0.f};
@@ -1260,7 +1267,7 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
         __syncthreads();
         for (int i = tid; i < p; i += NTHREADS) rhsa[i] = wv[m1 + i] + (T)(rl[i] - s[i]);
         __syncthreads();
-        chol_solve(p, Mb, ldM, rhsa, y, dla, tscr);
+        solve(rhsa, y, dla, tscr);
         mv_sym_upper(p, Mb, ldM, dM, dla, tmp, mdl, tscr);
         // Δs from the complementarity row where s ≤ λ and from the primal row
         // GΔz + Δs = −r_λ (with GΔz = RE·u − MΔλ) elsewhere: the first multiplies the
@@ -1291,7 +1298,7 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
           rhs[i] = rhsa[i] + cc / (T)lam[i];
         }
         __syncthreads();
-        chol_solve(p, Mb, ldM, rhs, y, dl, tscr);
+        solve(rhs, y, dl, tscr);
         mv_cols(SR + (size_t)m1 * ldS, ldS, p, m1, TRI_ALL, dl, tscr,
                 [&](int c, T val) { dzn[c] = wv[c] - val; });
         mv_sym_upper(p, Mb, ldM, dM, dl, tmp, mdl, tscr);
@@ -1394,7 +1401,8 @@ __device__ __forceinline__ void fwd_smem_path(const FwdInst<T>& I, unsigned char
       [&](const T* Qb, const T* Ab, const T* Gb) {
         return sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
       },
-      [&](const T* dsh) { return chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb); });
+      [&](const T* dsh) { return chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb); },
+      [&](const T* rhs, T* y, T* out, T* scr) { chol_solve(p, Mb, L.ldM, rhs, y, out, scr); });
 }
 
 // One instance on the global-memory path (factors in the workspace, see qp_large.cuh).
@@ -1421,9 +1429,14 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
         const int NT = (p + 3) >> 2, nt = NT * (NT + 1) / 2, ldM = p > 0 ? p : 1;
         if (nt <= NTHREADS) return chol_inv<T, 1>(p, Mb, ldM, dM, dsh, cb);
         if constexpr (sizeof(T) == 4) {
-          if (nt <= 2 * NTHREADS && p <= REG_CHOL_MAX_P) return chol_inv<T, 2>(p, Mb, ldM, dM, dsh, cb);
+          if (reg_chol_ok(p, 4)) return chol_inv<T, 2>(p, Mb, ldM, dM, dsh, cb);
         }
-        return gchol_inv<T>(p, Mb, dM, dsh, Aw, pan, L.pan_smem != 0, cb);
+        return gchol_factor<T>(p, Mb, dM, dsh, Aw, pan, L.pan_smem != 0, cb);
+      },
+      [&](const T* rhs, T* y, T* out, T* scr) {
+        const int ldM = p > 0 ? p : 1;
+        if (reg_chol_ok(p, (int)sizeof(T))) chol_solve(p, Mb, ldM, rhs, y, out, scr);
+        else blk_solve(p, Mb, ldM, rhs, y, out, scr);
       });
 }
 
@@ -1524,7 +1537,12 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   // K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z; 0; 0; 0]  (Eq. 11), reduced form.
   mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
   __syncthreads();
-  if (p > 0) chol_solve(p, X, p, wv + m1, y, dl, tscr);
+  // The global-memory path leaves a blocked factor instead of X for large p.
+  const bool blk = P.large && !reg_chol_ok(p, (int)sizeof(T));
+  if (p > 0) {
+    if (blk) blk_solve(p, X, p, wv + m1, y, dl, tscr);
+    else chol_solve(p, X, p, wv + m1, y, dl, tscr);
+  }
   mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
           [&](int c, T val) { dzn[c] = wv[c] - val; });
   if (p == 0)
@@ -1563,7 +1581,10 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     __syncthreads();
     for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] + (T)rl[i];
     __syncthreads();
-    if (p > 0) chol_solve(p, X, p, rhs, y, dl, tscr);
+    if (p > 0) {
+      if (blk) blk_solve(p, X, p, rhs, y, dl, tscr);
+      else chol_solve(p, X, p, rhs, y, dl, tscr);
+    }
     mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
             [&](int c, T val) { dzn[c] = wv[c] - val; });
     if (p == 0)

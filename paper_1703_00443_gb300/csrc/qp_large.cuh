@@ -222,13 +222,14 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
 
 // Pivot block of the global-memory Cholesky, in registers of warp 0 (lane r holds row r of
 // the block): L_KK from the block column staged in Sb (Sb[c·ldp + i] = A(i, k0 + c)), and
-// V = L_KK⁻¹ written to sV (row-major NB × NB).  Rows beyond nb are the identity.  Each
-// column step shifts the row left by one, so the pivot column is always a[0] and the loop
-// needs no unrolling; pivots and rows travel by shuffles.  flag[0] = 1 on a non-positive or
+// V = L_KK⁻¹ written to sV (row-major NB × NB) and to the lower triangle of the diagonal block
+// of Mb (rows and columns k0..k0+nb−1).  Rows beyond nb are the identity.  Each column step
+// shifts the row left by one, so the pivot column is always a[0] and the loop needs no
+// unrolling; pivots and rows travel by shuffles.  flag[0] = 1 on a non-positive or
 // non-finite pivot.
 template <typename T, int NB>
 __device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int ldp, T* sV,
-                                               int* flag) {
+                                               T* Mb, int ldM, int* flag) {
   static_assert(NB <= 32, "one lane per row");
   const int r = threadIdx.x & 31;
   T a[NB], x[NB];
@@ -261,39 +262,42 @@ __device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int 
   }
   if (r < NB) {
 #pragma unroll
-    for (int c = 0; c < NB; ++c) sV[r * NB + c] = x[c];
+    for (int c = 0; c < NB; ++c) {
+      sV[r * NB + c] = x[c];
+      if (r < nb && c <= r) Mb[(size_t)(k0 + r) * ldM + k0 + c] = x[c];
+    }
   }
   if (r == 0) flag[0] = good ? 0 : 1;
 }
 
-// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ, with X = L⁻¹ built in the lower triangle
-// of Mb (whose strict upper triangle keeps M).  The trailing matrix lives in the global work
-// matrix Aw (lower triangle, row stride round4(p)); the current block column, the panel and
-// the pivot inverse live in shared memory (or, for very large p, in the global `pan`).
-// Block K = columns [k0, k0 + NB), t0 = k0 + NB, with block column K staged in S:
+// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ for Schur complements too large for the
+// register tiles.  The factor is left in the lower triangle of Mb (whose strict upper
+// triangle keeps M): the inverted diagonal blocks V_K = L_KK⁻¹ and, below them, the panels
+// L_IK; blk_solve applies it.  The trailing matrix lives in the global work matrix Aw (lower
+// triangle, row stride round4(p)); the current block column S, the panel P and V live in
+// shared memory (or, for very large p, S and P in the global `pan`).
+// Block K = columns [k0, k0 + NB), t0 = k0 + NB, block column K staged in S:
 //   A: warp 0 factors the diagonal block from S and inverts its factor, V = L_KK⁻¹;
-//   B: the panel P (NB rows of ld round8(p)) receives, by column range,
-//        P[c][j] = (V X_K·)[c][j]  for j < t0   (new block row of X),
-//        P[c][i] = (A_IK Vᵀ)[i][c] for i ≥ t0  (the panel L_IK, A_IK read from S);
-//   C: the new block row of X is copied from P to Mb (after B, whose items read the old
-//      one), and every lower-triangle entry (i ≥ t0, j ≤ i) takes
-//      C(i, j) −= Σ_c P[c][i] P[c][j], which is A_IJ −= L_IK L_JKᵀ for j ≥ t0 and
-//      X_IJ −= L_IK X_KJ for j < t0, over the tiles of that region only, in 8×4 register
-//      micro-tiles (tile row R, rows 8R..8R+7, holds the 2R + 2 tiles of columns 0..8R+7).
-//      Tiles of block column K + 1 go to S instead of Aw: they are final and only the next
-//      pivot block and panel read them.
+//   B: P[c][i] = (A_IK Vᵀ)[i][c] for i ≥ t0 (the panel L_IK, also stored to Mb);
+//   C: every lower-triangle entry of the trailing matrix takes A_IJ −= L_IK L_JKᵀ in 8×4
+//      register micro-tiles (tile row t0/8 + R holds the 2R + 2 tiles of columns
+//      t0..t0+8R+7).  Tiles of block column K + 1 go to S instead of Aw: they are final and
+//      only the next pivot block and panel read them.  Warp 0 takes the tiles of the next
+//      diagonal block and then runs step A of block K + 1 while the other warps finish C.
 // NB is 32 for FP32 and 16 for FP64 (register room of the pivot block).  Returns false on
 // every thread on a non-positive pivot.
 template <typename T>
-__device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, T* Aw, T* pan,
-                                       bool pan_in_sm, T* sm) {
+__device__ __noinline__ bool gchol_factor(int p, T* Mb, const T* dM, const T* dsh, T* Aw,
+                                          T* pan, bool pan_in_sm, T* sm) {
   constexpr int NB = chol_nb((int)sizeof(T));
-  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int ND = (NB / 8) * (NB / 8 + 1);      // tiles of one diagonal block
+  static_assert(ND <= 32, "one diagonal tile per lane of warp 0");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ldM = p > 0 ? p : 1, ldA = round4(p), ldp = (p + 7) & ~7;
-  const bool xvec = (p & 3) == 0;                   // rows of Mb 16-byte aligned
+  const bool mvec = (p & 3) == 0;                   // rows of Mb 16-byte aligned
   T* sV = sm;                                       // V (NB × NB)
   int* flag = reinterpret_cast<int*>(sm + NB * NB);
-  T* P = pan_in_sm ? sm + NB * NB + 16 : pan;       // panel: P[c·ldp + j]
+  T* P = pan_in_sm ? sm + NB * NB + 16 : pan;       // panel: P[c·ldp + i]
   T* S = P + (size_t)NB * ldp;                      // block column: S[c·ldp + i] = A(i, k0 + c)
 
   for (int e = tid; e < p * p; e += NTHREADS) {
@@ -302,28 +306,21 @@ __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, 
     const T v = (i == j) ? dM[i] + dsh[i] : Mb[(size_t)j * ldM + i];
     if (j < NB) S[(size_t)j * ldp + i] = v;
     else Aw[(size_t)i * ldA + j] = v;
-    Mb[e] = (i == j) ? T(1) : T(0);
   }
+  __syncthreads();
+  if (warp == 0) gchol_pivot_block<T, NB>(0, min(NB, p), S, ldp, sV, Mb, ldM, flag);
   __syncthreads();
   for (int k0 = 0; k0 < p; k0 += NB) {
     const int nb = min(NB, p - k0), t0 = k0 + nb;
-    if (warp == 0) gchol_pivot_block<T, NB>(k0, nb, S, ldp, sV, flag);
-    __syncthreads();
     if (flag[0]) return false;
-    // Phase B: work item (g, j) forms outputs c = 8g..8g+7 of panel column j (the X block row
-    // for j < t0, the L panel for j ≥ t0); j runs fastest so V is read by broadcast.
-    for (int w = tid; w < p * (NB / 8); w += NTHREADS) {
-      const int g = w / p, j = w - g * p;
+    // Phase B: work item (g, i) forms outputs c = 8g..8g+7 of panel row i; i runs fastest so
+    // V is read by broadcast.
+    const int nrow = p - t0;
+    for (int w = tid; w < nrow * (NB / 8); w += NTHREADS) {
+      const int g = w / nrow, i = t0 + (w - g * nrow);
       T v[NB];
-      if (j < t0) {
 #pragma unroll
-        for (int q = 0; q < NB; ++q)
-          v[q] = (q < nb && j <= k0 + q) ? Mb[(size_t)(k0 + q) * ldM + j] : T(0);
-      } else {
-#pragma unroll
-        for (int q = 0; q < NB; ++q) v[q] = (q < nb) ? S[(size_t)q * ldp + j] : T(0);
-      }
-      // X row: P[c][j] = Σ_q V[c][q] X[k0+q][j];  L panel: P[c][j] = Σ_q A[j][k0+q] V[c][q].
+      for (int q = 0; q < NB; ++q) v[q] = S[(size_t)q * ldp + i];
       T acc[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] = T(0);
@@ -340,41 +337,40 @@ __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, 
         }
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e) P[(size_t)(8 * g + e) * ldp + j] = acc[e];
+      for (int e = 0; e < 8; ++e) P[(size_t)(8 * g + e) * ldp + i] = acc[e];
+      T* mrow = Mb + (size_t)i * ldM + k0 + 8 * g;
+      if (mvec) {
+        st4(mrow, acc[0], acc[1], acc[2], acc[3]);
+        st4(mrow + 4, acc[4], acc[5], acc[6], acc[7]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) mrow[e] = acc[e];
+      }
     }
     __syncthreads();
-    for (int e = tid; e < nb * t0; e += NTHREADS) {
-      const int c = e / t0, j = e - c * t0;
-      if (j <= k0 + c) Mb[(size_t)(k0 + c) * ldM + j] = P[(size_t)c * ldp + j];
-    }
-    // Phase C: lower-triangle 8×4 tiles of rows [t0, p) (t0 is a multiple of 8).
+    // Phase C, with step A of block K + 1 overlapped in warp 0.
     if (t0 < p) {
-      const int R0 = t0 >> 3, R1 = (p + 7) >> 3, t1 = t0 + NB;
-      const long long base = (long long)R0 * (R0 + 1);
-      const long long ntile = (long long)R1 * (R1 + 1) - base;
-      for (long long t = tid; t < ntile; t += NTHREADS) {
-        const long long u = t + base;   // tiles before tile row R: R(R + 1)
+      const int t1 = t0 + NB;
+      const long long ntile = (long long)((p - t0 + 7) >> 3) * (((p - t0 + 7) >> 3) + 1);
+      auto tile = [&](long long u) {
         int R = (int)((sqrtf(4.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
         while ((long long)(R + 1) * (R + 2) <= u) ++R;
         while ((long long)R * (R + 1) > u) --R;
-        const int ib = 8 * R, jb = 4 * (int)(u - (long long)R * (R + 1));
-        const bool isx = jb < t0, stage = !isx && jb < t1;
-        T* Cb = isx ? Mb : Aw;
-        const int ldc = isx ? ldM : ldA;
-        const bool vec = isx ? xvec : true;
+        const int ib = t0 + 8 * R, jb = t0 + 4 * (int)(u - (long long)R * (R + 1));
+        const bool stage = jb < t1;
         T c[32];
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr) {
           const int i = ib + rr;
-          if (vec && i < p && jb + 3 <= i) {
+          if (i < p && jb + 3 <= i) {
             T t4[4];
-            ld4(t4, Cb + (size_t)i * ldc + jb);
+            ld4(t4, Aw + (size_t)i * ldA + jb);
 #pragma unroll
             for (int q = 0; q < 4; ++q) c[rr * 4 + q] = t4[q];
           } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              c[rr * 4 + q] = (i < p && jb + q <= i) ? Cb[(size_t)i * ldc + jb + q] : T(0);
+              c[rr * 4 + q] = (i < p && jb + q <= i) ? Aw[(size_t)i * ldA + jb + q] : T(0);
           }
         }
 #pragma unroll 4
@@ -404,20 +400,124 @@ __device__ __noinline__ bool gchol_inv(int p, T* Mb, const T* dM, const T* dsh, 
 #pragma unroll
           for (int rr = 0; rr < 8; ++rr) {
             const int i = ib + rr;
-            if (vec && i < p && jb + 3 <= i) {
-              st4(Cb + (size_t)i * ldc + jb, c[rr * 4], c[rr * 4 + 1], c[rr * 4 + 2], c[rr * 4 + 3]);
+            if (i < p && jb + 3 <= i) {
+              st4(Aw + (size_t)i * ldA + jb, c[rr * 4], c[rr * 4 + 1], c[rr * 4 + 2], c[rr * 4 + 3]);
             } else {
 #pragma unroll
               for (int q = 0; q < 4; ++q)
-                if (i < p && jb + q <= i) Cb[(size_t)i * ldc + jb + q] = c[rr * 4 + q];
+                if (i < p && jb + q <= i) Aw[(size_t)i * ldA + jb + q] = c[rr * 4 + q];
             }
           }
         }
+      };
+      if (warp == 0) {
+        // The tiles of the next diagonal block come first in the order (tile rows 0..NB/8−1).
+        if (lane < ND && lane < ntile) tile(lane);
+        __syncwarp();
+        gchol_pivot_block<T, NB>(t0, min(NB, p - t0), S, ldp, sV, Mb, ldM, flag);
+      } else {
+        for (long long u = ND + (tid - 32); u < ntile; u += NTHREADS - 32) tile(u);
       }
     }
     __syncthreads();
   }
   return true;
+}
+
+// out = (L Lᵀ)⁻¹ rhs with the factor of gchol_factor in the lower triangle of Mb (inverted
+// diagonal blocks V_K, panels L_IK below them); y receives L⁻¹ rhs.  Forward substitution
+// y_K = V_K (rhs_K − Σ_{J<K} L_KJ y_J) by block rows, then back substitution
+// out_K = V_Kᵀ (y_K − Σ_{I>K} L_IKᵀ out_I) by block columns, two barriers per block each way.
+// In each block step every thread issues its loads of V_K (staged to shared memory, row
+// stride NB + 1) together with its partial-sum loads, eight at a time, so the step waits for
+// memory about once.  `scr` holds BLK_SOLVE_SCR elements; y, out and scr are shared memory;
+// ends with a barrier.
+constexpr int BLK_SOLVE_SCR = 32 + 32 * NWARPS + 32 * 33;
+static_assert(BLK_SOLVE_SCR * 8 <= 8 * 4 * NTHREADS, "solve scratch within the 16 KB work region");
+template <typename T>
+__device__ __noinline__ void blk_solve(int p, const T* Mb, int ldM, const T* rhs, T* y, T* out,
+                                       T* scr) {
+  constexpr int NB = chol_nb((int)sizeof(T));
+  constexpr int TPR = NTHREADS / NB;   // threads per row of the forward block step
+  constexpr int VS = NB + 1;           // row stride of the staged V_K
+  constexpr int VPT = (NB * NB + NTHREADS - 1) / NTHREADS;
+  static_assert(TPR == 16 || TPR == 32, "row groups within a warp");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* t = scr;                       // NB values
+  T* part = scr + 32;               // NWARPS × 32 partial sums
+  T* sVb = part + 32 * NWARPS;      // V_K, NB × VS
+  auto load_v = [&](int k0, int nb, T (&vv)[VPT]) {
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+      const int idx = tid + e * NTHREADS, r = idx / NB, q = idx - r * NB;
+      vv[e] = (idx < NB * NB && r < nb && q <= r) ? Mb[(size_t)(k0 + r) * ldM + k0 + q] : T(0);
+    }
+  };
+  auto store_v = [&](const T (&vv)[VPT]) {
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+      const int idx = tid + e * NTHREADS, r = idx / NB, q = idx - r * NB;
+      if (idx < NB * NB) sVb[r * VS + q] = vv[e];
+    }
+  };
+  for (int k0 = 0; k0 < p; k0 += NB) {
+    const int nb = min(NB, p - k0);
+    T vv[VPT];
+    load_v(k0, nb, vv);
+    {
+      const int r = tid / TPR, h = tid - r * TPR;
+      T acc = T(0);
+      if (r < nb) {
+        const T* row = Mb + (size_t)(k0 + r) * ldM;
+#pragma unroll 8
+        for (int j = h; j < k0; j += TPR) acc = fma(row[j], y[j], acc);
+      }
+#pragma unroll
+      for (int off = TPR / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (h == 0 && r < nb) t[r] = rhs[k0 + r] - acc;
+    }
+    store_v(vv);
+    __syncthreads();
+    if (warp == 0 && lane < nb) {
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < NB; ++q) v = fma(sVb[lane * VS + q], t[q], v);
+      y[k0 + lane] = v;
+    }
+    __syncthreads();
+  }
+  for (int k0 = ((p - 1) / NB) * NB; p > 0 && k0 >= 0; k0 -= NB) {
+    const int nb = min(NB, p - k0), t0 = k0 + nb;
+    const int c = (NB == 32) ? lane : (lane & 15);
+    T vv[VPT];
+    load_v(k0, nb, vv);
+    {
+      T acc = T(0);
+      const int rstep = (NB == 32) ? NWARPS : 2 * NWARPS;
+      const int r0 = (NB == 32) ? warp : 2 * warp + (lane >> 4);
+      if (c < nb) {
+#pragma unroll 8
+        for (int i = t0 + r0; i < p; i += rstep) acc = fma(Mb[(size_t)i * ldM + k0 + c], out[i], acc);
+      }
+      part[warp * 32 + lane] = acc;
+    }
+    store_v(vv);
+    __syncthreads();
+    if (warp == 0) {
+      T u = T(0);
+#pragma unroll
+      for (int w = 0; w < NWARPS; ++w) {
+        u += part[w * 32 + c];
+        if (NB != 32) u += part[w * 32 + 16 + c];
+      }
+      u = (c < nb) ? y[k0 + c] - u : T(0);
+      T x = T(0);
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x = fma(sVb[r * VS + c], __shfl_sync(0xffffffffu, u, r), x);
+      if (lane < nb && lane < NB) out[k0 + lane] = x;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace qpk
