@@ -145,7 +145,7 @@ struct FwdSmem {
       // The setup sweep's two 16-row panels (ld round8(m1 + p)) likewise, after its pivot
       // scratch, if they fit too.
       const size_t nb = (size_t)chol_nb((int)es);
-      const size_t pc = align_up((nb * nb + 16 + 2 * nb * (size_t)((p + 7) & ~7)) * es, 16);
+      const size_t pc = align_up(((2 * nb * nb + 2 * nb + 16) + 2 * nb * (size_t)((p + 7) & ~7)) * es, 16);
       const size_t sc = align_up((2 * 16 * 16 + 16 + 2 * 16 * (size_t)((N3 + 7) & ~7)) * es, 16);
       if (o + (pc > cbytes ? pc : cbytes) + tail <= LARGE_PANEL_SMEM_CAP) {
         pan_smem = 1;

@@ -220,24 +220,26 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
   return true;
 }
 
-// Pivot block of the global-memory Cholesky, in registers of warp 0 (lane r holds row r of
-// the block): L_KK from the block column staged in Sb (Sb[c·ldp + i] = A(i, k0 + c)), and
-// V = L_KK⁻¹ written to sV (row-major NB × NB) and to the lower triangle of the diagonal block
-// of Mb (rows and columns k0..k0+nb−1).  Rows beyond nb are the identity.  Each column step
-// shifts the row left by one, so the pivot column is always a[0] and the loop needs no
-// unrolling; pivots and rows travel by shuffles.  flag[0] = 1 on a non-positive or
-// non-finite pivot.
+// Shared scratch of gchol_factor before its panels (elements of T): two parity buffers of the
+// pivot block's factor columns and reciprocal pivots, and a flag word.
+__host__ __device__ constexpr int gchol_scratch(int nb) { return 2 * nb * nb + 2 * nb + 16; }
+
+// Cholesky of the pivot block of the global-memory factorisation, in registers of warp 0
+// (lane r holds row r): A_KK from the block column staged in Sb (Sb[c·ldp + i] = A(i, k0+c))
+// becomes L_KK, published by columns: sLT[k·NB + j] = L(k+1+j, k) for k+1+j < NB and 0
+// beyond (each column shifted up to start at its first sub-diagonal entry), and
+// sInv[k] = 1/L(k, k).  Rows beyond nb are the identity.  Each column step shifts the row
+// left by one, so the pivot column is always a[0] and the loop needs no unrolling; pivots and
+// columns travel by shuffles.  flag[0] = 1 on a non-positive or non-finite pivot.
 template <typename T, int NB>
-__device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int ldp, T* sV,
-                                               T* Mb, int ldM, int* flag) {
+__device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int ldp, T* sLT,
+                                               T* sInv, int* flag) {
   static_assert(NB <= 32, "one lane per row");
   const int r = threadIdx.x & 31;
-  T a[NB], x[NB];
+  T a[NB];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
+  for (int c = 0; c < NB; ++c)
     a[c] = (r < nb && c <= r) ? Sb[(size_t)c * ldp + k0 + r] : ((r == c) ? T(1) : T(0));
-    x[c] = (r == c) ? T(1) : T(0);
-  }
   bool good = true;
 #pragma unroll 1
   for (int k = 0; k < NB; ++k) {
@@ -245,6 +247,9 @@ __device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int 
     good = good && isfinite(d) && d > T(0);
     const T inv = rsqrt(d);
     const T l = (r > k) ? a[0] * inv : T(0);   // l_rk below the pivot
+    const T lsh = __shfl_down_sync(0xffffffffu, l, k + 1);
+    if (r < NB) sLT[k * NB + r] = (r + k + 1 < NB) ? lsh : T(0);
+    if (r == 0) sInv[k] = inv;
 #pragma unroll
     for (int jj = 1; jj < NB; ++jj) {
       const T lj = __shfl_sync(0xffffffffu, l, (k + jj) & 31);
@@ -253,37 +258,58 @@ __device__ __noinline__ void gchol_pivot_block(int k0, int nb, const T* Sb, int 
 #pragma unroll
     for (int jj = 0; jj + 1 < NB; ++jj) a[jj] = a[jj + 1];
     a[NB - 1] = T(0);
-    // Row k of V is final once divided by l_kk; the rows below eliminate it.
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const T xk = __shfl_sync(0xffffffffu, x[q], k) * inv;
-      x[q] = (r == k) ? xk : fma(-l, xk, x[q]);
-    }
-  }
-  if (r < NB) {
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      sV[r * NB + c] = x[c];
-      if (r < nb && c <= r) Mb[(size_t)(k0 + r) * ldM + k0 + c] = x[c];
-    }
   }
   if (r == 0) flag[0] = good ? 0 : 1;
+}
+
+// V_K = L_KK⁻¹ from the published columns of the pivot block (sLT, sInv), by one warp: lane c
+// forms column c by forward substitution, and the lower triangle of the diagonal block of Mb
+// (rows and columns k0..k0+nb−1) receives it.
+template <typename T, int NB>
+__device__ __noinline__ void gchol_invert_block(int k0, int nb, const T* sLT, const T* sInv,
+                                                T* Mb, int ldM) {
+  const int c = threadIdx.x & 31;
+  T x[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) x[r] = (r == c) ? T(1) : T(0);
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    x[q] *= sInv[q];   // V(q, c), zero above the diagonal
+#pragma unroll
+    for (int m4 = 0; q + 1 + 4 * m4 < NB; ++m4) {
+      T w[4];
+      ld4(w, sLT + q * NB + 4 * m4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = q + 1 + 4 * m4 + e;
+        if (r < NB) x[r] = fma(-w[e], x[q], x[r]);
+      }
+    }
+  }
+  if (c < nb) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r >= c && r < nb) Mb[(size_t)(k0 + r) * ldM + k0 + c] = x[r];
+  }
 }
 
 // Blocked Cholesky factorisation M + D(dsh) = L Lᵀ for Schur complements too large for the
 // register tiles.  The factor is left in the lower triangle of Mb (whose strict upper
 // triangle keeps M): the inverted diagonal blocks V_K = L_KK⁻¹ and, below them, the panels
 // L_IK; blk_solve applies it.  The trailing matrix lives in the global work matrix Aw (lower
-// triangle, row stride round4(p)); the current block column S, the panel P and V live in
-// shared memory (or, for very large p, S and P in the global `pan`).
+// triangle, row stride round4(p)); the current block column S, the panel P and the pivot
+// block's columns live in shared memory (or, for very large p, S and P in the global `pan`).
 // Block K = columns [k0, k0 + NB), t0 = k0 + NB, block column K staged in S:
-//   A: warp 0 factors the diagonal block from S and inverts its factor, V = L_KK⁻¹;
-//   B: P[c][i] = (A_IK Vᵀ)[i][c] for i ≥ t0 (the panel L_IK, also stored to Mb);
+//   A: warp 0 factors the diagonal block from S (gchol_pivot_block);
+//   B: one thread per row i ≥ t0 solves L_KK l_iᵀ = a_iᵀ (row i of the panel L_IK) by forward
+//      substitution, shifting the row through registers so the results come out in order;
+//      P[c][i] and Mb[i][k0 + c] receive it;
 //   C: every lower-triangle entry of the trailing matrix takes A_IJ −= L_IK L_JKᵀ in 8×4
 //      register micro-tiles (tile row t0/8 + R holds the 2R + 2 tiles of columns
 //      t0..t0+8R+7).  Tiles of block column K + 1 go to S instead of Aw: they are final and
-//      only the next pivot block and panel read them.  Warp 0 takes the tiles of the next
-//      diagonal block and then runs step A of block K + 1 while the other warps finish C.
+//      only the next pivot block and panel read them.  Meanwhile warp 0 takes the tiles of the
+//      next diagonal block and then runs step A of block K + 1, and warp 1 inverts L_KK into
+//      the diagonal block of Mb (the pivot columns are double-buffered by block parity).
 // NB is 32 for FP32 and 16 for FP64 (register room of the pivot block).  Returns false on
 // every thread on a non-positive pivot.
 template <typename T>
@@ -295,9 +321,10 @@ __device__ __noinline__ bool gchol_factor(int p, T* Mb, const T* dM, const T* ds
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ldM = p > 0 ? p : 1, ldA = round4(p), ldp = (p + 7) & ~7;
   const bool mvec = (p & 3) == 0;                   // rows of Mb 16-byte aligned
-  T* sV = sm;                                       // V (NB × NB)
-  int* flag = reinterpret_cast<int*>(sm + NB * NB);
-  T* P = pan_in_sm ? sm + NB * NB + 16 : pan;       // panel: P[c·ldp + i]
+  T* sLT = sm;                                      // 2 × NB × NB pivot columns
+  T* sInv = sm + 2 * NB * NB;                       // 2 × NB reciprocal pivots
+  int* flag = reinterpret_cast<int*>(sm + 2 * NB * NB + 2 * NB);
+  T* P = pan_in_sm ? sm + gchol_scratch(NB) : pan;  // panel: P[c·ldp + i]
   T* S = P + (size_t)NB * ldp;                      // block column: S[c·ldp + i] = A(i, k0 + c)
 
   for (int e = tid; e < p * p; e += NTHREADS) {
@@ -308,47 +335,46 @@ __device__ __noinline__ bool gchol_factor(int p, T* Mb, const T* dM, const T* ds
     else Aw[(size_t)i * ldA + j] = v;
   }
   __syncthreads();
-  if (warp == 0) gchol_pivot_block<T, NB>(0, min(NB, p), S, ldp, sV, Mb, ldM, flag);
+  if (warp == 0) gchol_pivot_block<T, NB>(0, min(NB, p), S, ldp, sLT, sInv, flag);
   __syncthreads();
-  for (int k0 = 0; k0 < p; k0 += NB) {
+  for (int k0 = 0, par = 0; k0 < p; k0 += NB, par ^= 1) {
     const int nb = min(NB, p - k0), t0 = k0 + nb;
+    const T* cLT = sLT + par * NB * NB;
+    const T* cInv = sInv + par * NB;
     if (flag[0]) return false;
-    // Phase B: work item (g, i) forms outputs c = 8g..8g+7 of panel row i; i runs fastest so
-    // V is read by broadcast.
-    const int nrow = p - t0;
-    for (int w = tid; w < nrow * (NB / 8); w += NTHREADS) {
-      const int g = w / nrow, i = t0 + (w - g * nrow);
-      T v[NB];
+    // Phase B: row i of the panel by forward substitution with L_KK.
+    for (int i = t0 + tid; i < p; i += NTHREADS) {
+      T a[NB];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) v[q] = S[(size_t)q * ldp + i];
-      T acc[8];
+      for (int q = 0; q < NB; ++q) a[q] = S[(size_t)q * ldp + i];
+#pragma unroll 1
+      for (int c = 0; c < NB; ++c) {
+        const T l = a[0] * cInv[c];
+        const T* col = cLT + c * NB;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) acc[e] = T(0);
+        for (int j = 0; j + 1 < NB; j += 4) {
+          T w[4];
+          ld4(w, col + j);
 #pragma unroll
-      for (int q = 0; q < NB; q += 4) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          T wv[4];
-          ld4(wv, sV + (8 * g + e) * NB + q);
-          acc[e] = fma(wv[0], v[q], acc[e]);
-          acc[e] = fma(wv[1], v[q + 1], acc[e]);
-          acc[e] = fma(wv[2], v[q + 2], acc[e]);
-          acc[e] = fma(wv[3], v[q + 3], acc[e]);
+          for (int e = 0; e < 4; ++e)
+            if (j + e + 1 < NB) a[j + e] = fma(-l, w[e], a[j + e + 1]);
         }
+        a[NB - 1] = l;
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e) P[(size_t)(8 * g + e) * ldp + i] = acc[e];
-      T* mrow = Mb + (size_t)i * ldM + k0 + 8 * g;
+      for (int c = 0; c < NB; ++c) P[(size_t)c * ldp + i] = a[c];
+      T* mrow = Mb + (size_t)i * ldM + k0;
       if (mvec) {
-        st4(mrow, acc[0], acc[1], acc[2], acc[3]);
-        st4(mrow + 4, acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+        for (int c = 0; c < NB; c += 4) st4(mrow + c, a[c], a[c + 1], a[c + 2], a[c + 3]);
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) mrow[e] = acc[e];
+        for (int c = 0; c < NB; ++c) mrow[c] = a[c];
       }
     }
     __syncthreads();
-    // Phase C, with step A of block K + 1 overlapped in warp 0.
+    // Phase C, with step A of block K + 1 in warp 0 and the inverse of L_KK in warp 1.
+    if (warp == 1) gchol_invert_block<T, NB>(k0, nb, cLT, cInv, Mb, ldM);
     if (t0 < p) {
       const int t1 = t0 + NB;
       const long long ntile = (long long)((p - t0 + 7) >> 3) * (((p - t0 + 7) >> 3) + 1);
@@ -414,9 +440,10 @@ __device__ __noinline__ bool gchol_factor(int p, T* Mb, const T* dM, const T* ds
         // The tiles of the next diagonal block come first in the order (tile rows 0..NB/8−1).
         if (lane < ND && lane < ntile) tile(lane);
         __syncwarp();
-        gchol_pivot_block<T, NB>(t0, min(NB, p - t0), S, ldp, sV, Mb, ldM, flag);
-      } else {
-        for (long long u = ND + (tid - 32); u < ntile; u += NTHREADS - 32) tile(u);
+        gchol_pivot_block<T, NB>(t0, min(NB, p - t0), S, ldp, sLT + (par ^ 1) * NB * NB,
+                                 sInv + (par ^ 1) * NB, flag);
+      } else if (warp >= 2) {
+        for (long long u = ND + (tid - 64); u < ntile; u += NTHREADS - 64) tile(u);
       }
     }
     __syncthreads();
