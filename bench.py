@@ -205,10 +205,10 @@ def cpu_baseline(n, p, m, budget_s=15.0, gpu_out=None):
     return res, acc
 
 
-def serving_run(dev, rate, count):
-    """Poisson stream of fwd+bwd requests (n log-uniform in [16, 512], nineq = n, neq = n/4)
-    through the continuous-batching server; p50/p99 latency from arrival to result."""
-    import torch
+def serving_run(dev, rates, count):
+    """Poisson streams of fwd+bwd requests (n log-uniform in [16, 512], nineq = n, neq = n/4)
+    through the continuous-batching server, one run per offered rate; p50/p99 latency from
+    arrival to result, throughput, and the scheduler's host time per batch."""
     from paper_1703_00443_gb300 import inputs
     from paper_1703_00443_gb300.serving import QPServer, poisson_run
     sizes = inputs.serve_sizes(128)
@@ -218,19 +218,25 @@ def serving_run(dev, rate, count):
         gg = inputs.upstream_grad(1, nn, workload=inputs.WL_SERVE, start=i)[0]
         pool.append((tuple(np.float32(x) for x in data), np.float32(gg)))
     server = QPServer(device=dev, max_inflight=4, max_batch=512)
+    runs = []
     try:
-        poisson_run(server, pool[:16], rate, min(64, count))       # warm-up
-        server.latencies.clear()
-        server.batch_sizes.clear()
-        server.completed = 0
-        results, wall = poisson_run(server, pool, rate, count, seed=1)
-        st = server.stats()
+        poisson_run(server, pool[:16], rates[0], min(64, count))       # warm-up
+        for k, rate in enumerate(rates):
+            server.latencies.clear()
+            server.batch_sizes.clear()
+            server.completed = 0
+            server.host_s = {"launch": 0.0, "retire": 0.0}
+            results, wall = poisson_run(server, pool, rate, count, seed=1 + k)
+            st = server.stats()
+            bad = sum(r["status"] != 0 for r in results)
+            runs.append({"rate_req_s": rate, "requests": count, "throughput_req_s": count / wall,
+                         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"],
+                         "mean_batch": st["mean_batch"], "nonconverged": int(bad),
+                         "host_ms_per_batch": st["host_launch_ms_per_batch"] +
+                         st["host_retire_ms_per_batch"]})
     finally:
         server.close()
-    bad = sum(r["status"] != 0 for r in results)
-    return {"rate_req_s": rate, "requests": count, "throughput_req_s": count / wall,
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"],
-            "mean_batch": st["mean_batch"], "nonconverged": int(bad),
+    return {"runs": runs, "max_inflight": 4,
             "workload": "n log-uniform [16,512], nineq=n, neq=n/4, fwd+bwd, host arrays in/out"}
 
 
@@ -397,7 +403,8 @@ def run_gpu(args):
                "dQ": gout[0].cpu().numpy()}
     served = None
     if not args.no_extras and ws == 1:
-        served = serving_run(dev, args.serve_rate, args.serve_count)
+        served = serving_run(dev, [float(r) for r in str(args.serve_rate).split(",")],
+                             args.serve_count)
     cpu, acc = (None, None)
     if not args.no_cpu_baseline and ws == 1:
         cpu, acc = cpu_baseline(n, p, m, budget_s=args.cpu_budget, gpu_out=gpu_out)
@@ -550,7 +557,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the packed and serving runs")
-    ap.add_argument("--serve-rate", type=float, default=5000.0)
+    ap.add_argument("--serve-rate", default="1000,3000,10000",
+                    help="offered request rates (req/s), comma-separated")
     ap.add_argument("--serve-count", type=int, default=1000)
     ap.add_argument("--workload", default="headline", choices=["headline", "sweep", "onehot", "uneven"])
     ap.add_argument("--uneven-count", type=int, default=4096)

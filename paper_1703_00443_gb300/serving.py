@@ -10,6 +10,10 @@ When a batch's completion event fires, its results are copied to the host, every
 future is resolved with its own z*, λ*, ν* and gradients, and the batch's slot and budget are
 released.  Latency is measured from each request's arrival to the resolution of its future.
 
+Each stream slot keeps one pinned host buffer for a batch's inputs and one for its results,
+grown on demand and reused: a batch is packed into sections of the input buffer with numpy
+slice copies and moves to the device in one copy, and all its results come back in one copy.
+
 Each instance is solved by one thread block on the kernel path its own size selects, so a
 request's result does not depend on what it was batched with.
 """
@@ -24,7 +28,7 @@ import time
 import numpy as np
 import torch
 
-from .packed import PackedBatch
+from .packed import PackedBatch, PackedForward
 from .qp import default_options, workspace_bytes
 
 GRAD_KEYS = ("dQ", "dq", "dG", "dh", "dA", "db")
@@ -82,13 +86,46 @@ class Admission:
         self.reserved -= int(nbytes)
 
 
+def _sections(sizes, align=64):
+    """Offsets of consecutive sections of the given element counts (each at least 1), every
+    section starting on a multiple of ``align`` elements; returns (offsets, total)."""
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += (max(int(n), 1) + align - 1) // align * align
+    return offs, o
+
+
+class _Staging:
+    """Pinned host buffers of one stream slot, grown on demand (doubling) and reused."""
+
+    def __init__(self, dtype):
+        self.dtype = dtype
+        self.inp = torch.empty(0, dtype=dtype)
+        self.out = torch.empty(0, dtype=dtype)
+        self.status = torch.empty(0, dtype=torch.int32)
+
+    @staticmethod
+    def _grow(buf, n, dtype):
+        if buf.numel() >= n:
+            return buf
+        return torch.empty(max(n, 2 * buf.numel()), dtype=dtype, pin_memory=True)
+
+    def reserve(self, n_in, n_out, n_status):
+        self.inp = self._grow(self.inp, n_in, self.dtype)
+        self.out = self._grow(self.out, n_out, self.dtype)
+        self.status = self._grow(self.status, n_status, torch.int32)
+
+
 class QPServer:
-    def __init__(self, device="cuda:0", dtype=torch.float32, max_inflight=3, max_batch=1024,
+    def __init__(self, device="cuda:0", dtype=torch.float32, max_inflight=4, max_batch=1024,
                  hbm_budget_bytes=8 << 30, options=None):
         self.device = torch.device(device)
         self.dtype = dtype
         self.options = options if options is not None else default_options(dtype)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(max_inflight)]
+        self.staging = [_Staging(dtype) for _ in range(max_inflight)]
+        self.host_s = {"launch": 0.0, "retire": 0.0}
         self.free_streams = list(range(max_inflight))
         self.admission = Admission(hbm_budget_bytes, max_batch)
         self.queue = collections.deque()
@@ -98,11 +135,14 @@ class QPServer:
         self.batch_sizes = []
         self.completed = 0
         self._stop = False
+        self._error = None
         self._thread = threading.Thread(target=self._loop, daemon=True)
         self._thread.start()
 
     # ------------------------------------------------------------------ client side
     def submit(self, Q, q, G, h, A, b, dl_dz, arrival=None) -> concurrent.futures.Future:
+        if self._error is not None:
+            raise RuntimeError(f"QP server scheduler failed: {self._error!r}")
         npdt = np.float32 if self.dtype == torch.float32 else np.float64
         data = tuple(np.ascontiguousarray(np.asarray(x), dtype=npdt) for x in (Q, q, G, h, A, b))
         fut = concurrent.futures.Future()
@@ -122,60 +162,97 @@ class QPServer:
 
     def stats(self):
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        nb = max(len(self.batch_sizes), 1)
         return {"completed": self.completed, "batches": len(self.batch_sizes),
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "host_launch_ms_per_batch": 1e3 * self.host_s["launch"] / nb,
+                "host_retire_ms_per_batch": 1e3 * self.host_s["retire"] / nb}
 
     # ------------------------------------------------------------------ scheduler
     def _launch(self, reqs, sidx):
-        stream = self.streams[sidx]
+        t0 = time.perf_counter()
+        stream, stg = self.streams[sidx], self.staging[sidx]
         dims = [r.dims for r in reqs]
+        keys = PackedBatch.KEYS
         with torch.cuda.stream(stream):
             pb = PackedBatch(dims, dtype=self.dtype, device=self.device, options=self.options)
-            host = []
-            for j, key in enumerate(pb.KEYS):
-                buf = torch.zeros(max(pb.totals[key], 1), dtype=self.dtype).pin_memory()
+            tot = pb.totals
+            # inputs: Q q G h A b and dℓ/dz; results: z λ ν and the six gradients
+            isec, n_in = _sections([tot[k] for k in keys] + [tot["q"]])
+            osec, n_out = _sections([tot["q"], tot["h"], tot["b"]] + [tot[k] for k in keys])
+            stg.reserve(n_in, n_out, len(reqs))
+            hin = stg.inp.numpy()
+            hin[:n_in] = 0
+            for j, key in enumerate(keys):
+                base = isec[j]
                 for o, l, r in zip(pb.offsets[key], pb.lengths[key], reqs):
                     if l:
-                        buf[o:o + l] = torch.from_numpy(r.data[j].reshape(-1))
-                host.append(buf)
-            gbuf = torch.zeros(max(pb.totals["q"], 1), dtype=self.dtype).pin_memory()
+                        hin[base + o:base + o + l] = r.data[j].reshape(-1)
+            gbase = isec[len(keys)]
             for o, l, r in zip(pb.offsets["q"], pb.lengths["q"], reqs):
-                gbuf[o:o + l] = torch.from_numpy(r.dl_dz.reshape(-1))
-            dev = [t.to(self.device, non_blocking=True) for t in host]
-            g = gbuf.to(self.device, non_blocking=True)
-            Q, q, G, h, A, b = dev
-            out = pb.forward(Q, q, G, h, A, b)
-            grads = pb.backward(Q, G, A, g)
-            res = {"z": out.z.to("cpu", non_blocking=True), "lam": out.lam.to("cpu", non_blocking=True),
-                   "nu": out.nu.to("cpu", non_blocking=True),
-                   "status": out.status.to("cpu", non_blocking=True)}
-            for k, t in zip(GRAD_KEYS, grads):
-                res[k] = t.to("cpu", non_blocking=True)
+                hin[gbase + o:gbase + o + l] = r.dl_dz.reshape(-1)
+            dev_in = torch.empty(n_in, dtype=self.dtype, device=self.device)
+            dev_in.copy_(stg.inp[:n_in], non_blocking=True)
+            view = lambda buf, off, n: buf[off:off + max(int(n), 1)]  # noqa: E731
+            Q, q, G, h, A, b = (view(dev_in, isec[j], tot[k]) for j, k in enumerate(keys))
+            g = view(dev_in, gbase, tot["q"])
+            dev_out = torch.zeros(n_out, dtype=self.dtype, device=self.device)
+            nB = max(len(reqs), 1)
+            fo = PackedForward(view(dev_out, osec[0], tot["q"]), view(dev_out, osec[1], tot["h"]),
+                               view(dev_out, osec[2], tot["b"]),
+                               torch.empty(nB, dtype=torch.int32, device=self.device),
+                               torch.empty(nB, dtype=torch.int32, device=self.device),
+                               torch.empty((nB, 4), dtype=torch.float64, device=self.device))
+            pb.forward(Q, q, G, h, A, b, out=fo)
+            grads = tuple(view(dev_out, osec[3 + j], tot[k]) for j, k in enumerate(keys))
+            pb.backward(Q, G, A, g, out=grads)
+            stg.out[:n_out].copy_(dev_out, non_blocking=True)
+            stg.status[:len(reqs)].copy_(fo.status[:len(reqs)], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
-        return {"reqs": reqs, "pb": pb, "res": res, "event": ev, "stream": sidx,
-                "keep": (host, gbuf, dev, g, out, grads)}
+        self.host_s["launch"] += time.perf_counter() - t0
+        return {"reqs": reqs, "pb": pb, "osec": osec, "event": ev, "stream": sidx,
+                "keep": (dev_in, dev_out, fo)}
 
     def _retire(self, item):
-        pb, res, reqs = item["pb"], item["res"], item["reqs"]
+        t0 = time.perf_counter()
+        pb, reqs, osec = item["pb"], item["reqs"], item["osec"]
+        stg = self.staging[item["stream"]]
+        hout = stg.out.numpy()
+        status = stg.status.numpy()
         now = time.perf_counter()
-        views = {"z": pb.unpack(res["z"], "q"), "lam": pb.unpack(res["lam"], "h"),
-                 "nu": pb.unpack(res["nu"], "b")}
-        for k, key in zip(GRAD_KEYS, pb.KEYS):
-            views[k] = pb.unpack(res[k], key)
-        status = res["status"].numpy()
+        fields = [("z", "q", osec[0]), ("lam", "h", osec[1]), ("nu", "b", osec[2])] + \
+            [(gk, k, osec[3 + j]) for j, (gk, k) in enumerate(zip(GRAD_KEYS, pb.KEYS))]
         for i, r in enumerate(reqs):
-            out = {k: views[k][i].numpy().copy() for k in views}
+            out = {}
+            for name, key, base in fields:
+                o, l = int(pb.offsets[key][i]), int(pb.lengths[key][i])
+                out[name] = hout[base + o:base + o + l].reshape(pb.shapes[key][i]).copy()
             out["status"] = int(status[i])
             self.latencies.append(now - r.arrival)
             r.future.set_result(out)
         self.completed += len(reqs)
         self.admission.release(sum(r.nbytes for r in reqs))
         self.free_streams.append(item["stream"])
+        self.host_s["retire"] += time.perf_counter() - t0
 
     def _loop(self):
+        try:
+            self._schedule()
+        except BaseException as exc:   # fail every pending request rather than leave it waiting
+            with self.cv:
+                pending = list(self.queue) + [r for item in self.inflight for r in item["reqs"]]
+                self.queue.clear()
+                self.inflight = []
+                self._error = exc
+            for r in pending:
+                if not r.future.done():
+                    r.future.set_exception(RuntimeError(f"QP server scheduler failed: {exc!r}"))
+            raise
+
+    def _schedule(self):
         torch.cuda.set_device(self.device)
         while True:
             with self.cv:
@@ -187,7 +264,8 @@ class QPServer:
             # retire finished batches
             for item in list(self.inflight):
                 if item["event"].query():
-                    self.inflight.remove(item)
+                    # by identity: items hold arrays, so == between them is not defined
+                    self.inflight = [x for x in self.inflight if x is not item]
                     self._retire(item)
                     progressed = True
             # admit new batches while slots and budget allow
@@ -207,7 +285,8 @@ class QPServer:
                 time.sleep(5e-5)
 
 
-def poisson_run(server: QPServer, pool, rate: float, count: int, seed: int = 0):
+def poisson_run(server: QPServer, pool, rate: float, count: int, seed: int = 0,
+                timeout: float = 600.0):
     """Drive ``server`` with ``count`` requests arriving as a Poisson stream of the given rate
     (requests cycle through ``pool``, a list of (data, dl_dz)).  Returns (results, wall_s)."""
     from .inputs import poisson_arrivals
@@ -224,5 +303,5 @@ def poisson_run(server: QPServer, pool, rate: float, count: int, seed: int = 0):
                 time.sleep(target - now - 1e-4)
         data, g = pool[k % len(pool)]
         futs.append(server.submit(*data, g, arrival=target))
-    results = [f.result() for f in futs]
+    results = [f.result(timeout=timeout) for f in futs]
     return results, time.perf_counter() - t0

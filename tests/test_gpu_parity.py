@@ -183,6 +183,39 @@ def test_global_memory_kernel_small_sizes(n, nineq, neq):
     _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
 
 
+@pytest.mark.parametrize("n,nineq,neq", [(60, 203, 10), (40, 180, 0), (24, 177, 7)])
+def test_global_memory_blocked_cholesky_fp32(n, nineq, neq):
+    """The global-memory kernel (forced) where the Schur complement is too large for the
+    register-tile Cholesky (nineq > 176): blocked factor with block-substitution solves,
+    including nineq not a multiple of 4 (unaligned rows of the factor) and of the block."""
+    from paper_1703_00443_gb300 import default_options
+    opts = default_options(torch.float32)
+    opts.path = 1
+    B = 2
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_PLAIN, dtype=np.float32,
+                                start=3000)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PLAIN, start=3000)
+    out = _run_opts(batch, g, np.float32, opts)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
+
+
+@pytest.mark.parametrize("n,nineq,neq", [(20, 40, 4), (30, 150, 5)])
+def test_global_memory_kernel_fp64(n, nineq, neq):
+    """The global-memory kernel (forced) in FP64: the register-tile Cholesky (nineq = 40) and
+    the blocked factor with 16-wide blocks (nineq = 150), at the FP64 tolerances."""
+    from paper_1703_00443_gb300 import default_options
+    opts = default_options(torch.float64)
+    opts.path = 1
+    B = 2
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_PLAIN, dtype=np.float64,
+                                start=4000)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PLAIN, dtype=np.float64, start=4000)
+    out = _run_opts(batch, g, np.float64, opts)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-9, 1e-8, ltol=1e-8)
+
+
 @pytest.mark.parametrize("n,nineq,neq", [(500, 500, 250), (256, 512, 64)])
 def test_global_memory_kernel_large_sizes(n, nineq, neq):
     """Sizes whose factors exceed shared memory: the timing sweep's n = 500 point and the

@@ -35,3 +35,40 @@ def test_fifo_order_is_kept_when_head_does_not_fit():
     q = _q([50, 10])
     b, rej, t = adm.take(q)
     assert b == [] and len(q) == 2      # the head waits; nothing overtakes it
+
+
+def test_scheduler_failure_fails_pending_requests_instead_of_hanging():
+    """If the scheduling thread raises, every queued and in-flight request's future gets the
+    error, and later submissions are refused (host logic only, no GPU)."""
+    import collections
+    import concurrent.futures
+    import threading
+
+    from paper_1703_00443_gb300.serving import QPServer, Request
+
+    srv = QPServer.__new__(QPServer)
+    srv.queue = collections.deque()
+    srv.inflight = []
+    srv.cv = threading.Condition()
+    srv._error = None
+    mk = lambda: Request((), None, 0.0, concurrent.futures.Future())  # noqa: E731
+    queued, running = [mk(), mk()], [mk()]
+    srv.queue.extend(queued)
+    srv.inflight.append({"reqs": running})
+
+    def boom():
+        raise ValueError("planted scheduler fault")
+
+    srv._schedule = boom
+    try:
+        srv._loop()
+    except ValueError:
+        pass
+    for r in queued + running:
+        assert isinstance(r.future.exception(timeout=1), RuntimeError)
+    assert not srv.queue and not srv.inflight
+    try:
+        srv.submit(None, None, None, None, None, None, None)
+        raise AssertionError("submit after a scheduler failure must raise")
+    except RuntimeError:
+        pass
