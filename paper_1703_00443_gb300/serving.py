@@ -13,6 +13,8 @@ released.  Latency is measured from each request's arrival to the resolution of 
 Each stream slot keeps one pinned host buffer for a batch's inputs and one for its results,
 grown on demand and reused: a batch is packed into sections of the input buffer with numpy
 slice copies and moves to the device in one copy, and all its results come back in one copy.
+The host copies (requests into the staging buffer, results out of it) run on a small thread
+pool: numpy releases the interpreter lock while it copies, so they proceed in parallel.
 
 Each instance is solved by one thread block on the kernel path its own size selects, so a
 request's result does not depend on what it was batched with.
@@ -86,6 +88,21 @@ class Admission:
         self.reserved -= int(nbytes)
 
 
+def _balanced(tasks, parts):
+    """Split (size, payload) tasks into ``parts`` lists of about equal total size."""
+    out, load = [[] for _ in range(parts)], [0] * parts
+    for t in sorted(tasks, key=lambda t: -t[0]):
+        k = load.index(min(load))
+        out[k].append(t[1])
+        load[k] += t[0]
+    return [c for c in out if c]
+
+
+def _copy_pairs(pairs):
+    for dst, src in pairs:
+        dst[...] = src
+
+
 def _sections(sizes, align=64):
     """Offsets of consecutive sections of the given element counts (each at least 1), every
     section starting on a multiple of ``align`` elements; returns (offsets, total)."""
@@ -99,10 +116,10 @@ def _sections(sizes, align=64):
 class _Staging:
     """Pinned host buffers of one stream slot, grown on demand (doubling) and reused."""
 
-    def __init__(self, dtype):
+    def __init__(self, dtype, elems=0):
         self.dtype = dtype
-        self.inp = torch.empty(0, dtype=dtype)
-        self.out = torch.empty(0, dtype=dtype)
+        self.inp = torch.empty(elems, dtype=dtype, pin_memory=elems > 0)
+        self.out = torch.empty(elems, dtype=dtype, pin_memory=elems > 0)
         self.status = torch.empty(0, dtype=torch.int32)
 
     @staticmethod
@@ -119,12 +136,17 @@ class _Staging:
 
 class QPServer:
     def __init__(self, device="cuda:0", dtype=torch.float32, max_inflight=4, max_batch=1024,
-                 hbm_budget_bytes=8 << 30, options=None):
+                 hbm_budget_bytes=8 << 30, options=None, staging_bytes=16 << 20,
+                 copy_threads=None):
         self.device = torch.device(device)
         self.dtype = dtype
         self.options = options if options is not None else default_options(dtype)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(max_inflight)]
-        self.staging = [_Staging(dtype) for _ in range(max_inflight)]
+        import os
+        self.copy_threads = int(copy_threads or min(8, os.cpu_count() or 1))
+        self.copier = concurrent.futures.ThreadPoolExecutor(self.copy_threads)
+        esz = 4 if dtype == torch.float32 else 8
+        self.staging = [_Staging(dtype, staging_bytes // esz) for _ in range(max_inflight)]
         self.host_s = {"launch": 0.0, "retire": 0.0}
         self.free_streams = list(range(max_inflight))
         self.admission = Admission(hbm_budget_bytes, max_batch)
@@ -159,6 +181,7 @@ class QPServer:
             self._stop = True
             self.cv.notify()
         self._thread.join()
+        self.copier.shutdown()
 
     def stats(self):
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
@@ -183,16 +206,17 @@ class QPServer:
             isec, n_in = _sections([tot[k] for k in keys] + [tot["q"]])
             osec, n_out = _sections([tot["q"], tot["h"], tot["b"]] + [tot[k] for k in keys])
             stg.reserve(n_in, n_out, len(reqs))
-            hin = stg.inp.numpy()
-            hin[:n_in] = 0
+            hin = stg.inp.numpy()   # gaps between instances are never read by the kernels
+            tasks = []
             for j, key in enumerate(keys):
                 base = isec[j]
                 for o, l, r in zip(pb.offsets[key], pb.lengths[key], reqs):
                     if l:
-                        hin[base + o:base + o + l] = r.data[j].reshape(-1)
+                        tasks.append((int(l), (hin[base + o:base + o + l], r.data[j].reshape(-1))))
             gbase = isec[len(keys)]
             for o, l, r in zip(pb.offsets["q"], pb.lengths["q"], reqs):
-                hin[gbase + o:gbase + o + l] = r.dl_dz.reshape(-1)
+                tasks.append((int(l), (hin[gbase + o:gbase + o + l], r.dl_dz.reshape(-1))))
+            list(self.copier.map(_copy_pairs, _balanced(tasks, self.copy_threads)))
             dev_in = torch.empty(n_in, dtype=self.dtype, device=self.device)
             dev_in.copy_(stg.inp[:n_in], non_blocking=True)
             view = lambda buf, off, n: buf[off:off + max(int(n), 1)]  # noqa: E731
@@ -213,14 +237,20 @@ class QPServer:
             ev = torch.cuda.Event()
             ev.record(stream)
         self.host_s["launch"] += time.perf_counter() - t0
-        return {"reqs": reqs, "pb": pb, "osec": osec, "event": ev, "stream": sidx,
+        return {"reqs": reqs, "pb": pb, "osec": osec, "n_out": n_out, "event": ev, "stream": sidx,
                 "keep": (dev_in, dev_out, fo)}
 
     def _retire(self, item):
         t0 = time.perf_counter()
         pb, reqs, osec = item["pb"], item["reqs"], item["osec"]
         stg = self.staging[item["stream"]]
-        hout = stg.out.numpy()
+        n_out = item["n_out"]
+        # one copy out of the staging buffer (in parallel ranges); each request's results view it
+        hout = np.empty(n_out, dtype=stg.out.numpy().dtype)
+        src = stg.out[:n_out].numpy()
+        step = (n_out + self.copy_threads - 1) // self.copy_threads
+        list(self.copier.map(_copy_pairs, [[(hout[a:a + step], src[a:a + step])]
+                                           for a in range(0, n_out, step)]))
         status = stg.status.numpy()
         now = time.perf_counter()
         fields = [("z", "q", osec[0]), ("lam", "h", osec[1]), ("nu", "b", osec[2])] + \
@@ -229,7 +259,7 @@ class QPServer:
             out = {}
             for name, key, base in fields:
                 o, l = int(pb.offsets[key][i]), int(pb.lengths[key][i])
-                out[name] = hout[base + o:base + o + l].reshape(pb.shapes[key][i]).copy()
+                out[name] = hout[base + o:base + o + l].reshape(pb.shapes[key][i])
             out["status"] = int(status[i])
             self.latencies.append(now - r.arrival)
             r.future.set_result(out)
