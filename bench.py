@@ -480,18 +480,20 @@ def run_workload(args):
             "data": "synthetic", "l2": "flushed between timed steps"}
     if args.workload == "sweep":
         rows = []
-        for n in (10, 50, 100, 500):
-            for B in (1, 64, 128):
-                p, m = n, n // 2
-                bt = inputs.random_batch(B, n, p, m, workload=inputs.WL_SWEEP)
-                g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
-                Tin = [torch.from_numpy(x).to(dev) for x in (bt.Q, bt.q, bt.G, bt.h, bt.A, bt.b)]
-                steps = 5 if n == 500 else 20
-                ms, f = _time_fixed(Tin, torch.from_numpy(g).to(dev), steps, flush, stream)
-                rows.append({"n": n, "nineq": p, "neq": m, "batch": B, "ms_per_step": ms,
-                             "solves_per_s": B / (ms / 1e3),
-                             "iters_mean": float(f.iters.float().mean()),
-                             "converged": int((f.status == 0).sum())})
+        grid = [(n, B) for n in (10, 50, 100, 500) for B in (1, 64, 128)]
+        if args.sweep_sizes:   # e.g. "500:1" for a one-launch profiling case
+            grid = [tuple(int(v) for v in item.split(":")) for item in args.sweep_sizes.split(",")]
+        for n, B in grid:
+            p, m = n, n // 2
+            bt = inputs.random_batch(B, n, p, m, workload=inputs.WL_SWEEP)
+            g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
+            Tin = [torch.from_numpy(x).to(dev) for x in (bt.Q, bt.q, bt.G, bt.h, bt.A, bt.b)]
+            steps = 5 if n == 500 else 20
+            ms, f = _time_fixed(Tin, torch.from_numpy(g).to(dev), steps, flush, stream)
+            rows.append({"n": n, "nineq": p, "neq": m, "batch": B, "ms_per_step": ms,
+                         "solves_per_s": B / (ms / 1e3),
+                         "iters_mean": float(f.iters.float().mean()),
+                         "converged": int((f.status == 0).sum())})
         line.update({"metric": "QP fwd+bwd solves/sec, timing sweep (n, nineq=n, neq=n/2)",
                      "sweep": rows})
     elif args.workload == "onehot":
@@ -562,6 +564,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=1000)
     ap.add_argument("--workload", default="headline", choices=["headline", "sweep", "onehot", "uneven"])
     ap.add_argument("--uneven-count", type=int, default=4096)
+    ap.add_argument("--sweep-sizes", default="",
+                    help="sweep points n:batch, comma-separated (default: the full grid)")
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--tuned", action="store_true", help="autotune the packed schedule first")
     args = ap.parse_args()
