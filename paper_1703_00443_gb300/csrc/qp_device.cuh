@@ -1132,7 +1132,7 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
   int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
   const int ldS = m1, ldM = p > 0 ? p : 1;
 
-  int status = ST_CONV, it = 0;
+  int status = ST_CONV, it = 0, extra = 0;
   float last[4] = {0.f, 0.f, 0.f, 0.f};   // residual norms and μ at the returned iterate
   bool ok = setup(Qb, Ab, Gb);
   __syncthreads();
@@ -1248,8 +1248,29 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
           break;
         }
         if (v[0] <= tz && v[1] <= tl && v[2] <= tn && mu <= mutol) {
-          status = ST_CONV;
-          break;
+          // FP32 path: also require every complementarity pair with max(λ_i, s_i) > 1e-5 to
+          // be resolved, min/max ≤ 1e-5 (at most 4 more iterations).  At finite μ a barely
+          // resolved pair keeps s_i/λ_i of order μ/max² instead of 0 or ∞ in the system the
+          // backward pass reuses, and the gradient inherits that bias; pairs below the floor
+          // (degenerate, both tending to 0) are exempt.
+          bool resolved = true;
+          if constexpr (sizeof(T) == 4) {
+            if (extra < 4) {
+              float w[4] = {0.f, 0.f, 0.f, 0.f};
+              for (int i = tid; i < p; i += NTHREADS) {
+                const float si = (float)s[i], li = (float)lam[i];
+                const float hi = fmaxf(si, li);
+                if (hi > 1e-5f) w[0] = fmaxf(w[0], fminf(si, li) / hi);
+              }
+              block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(w, red);
+              resolved = w[0] <= 1e-5f;
+              ++extra;
+            }
+          }
+          if (resolved) {
+            status = ST_CONV;
+            break;
+          }
         }
         if (it >= P.max_iter) {
           status = ST_MAXIT;

@@ -183,6 +183,23 @@ def test_global_memory_kernel_small_sizes(n, nineq, neq):
     _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
 
 
+def test_nearly_degenerate_instance_gradients_fp32():
+    """An instance of the n = 50 timing sweep whose most weakly resolved constraint has
+    max(λ_i, s_i) ≈ 5e-4 at the solution.  Its gradient is sensitive to how far the final
+    iterate resolves that pair (s_i/λ_i enters the system the backward pass solves), so the
+    FP32 path's stopping test also requires resolved complementarity pairs."""
+    B, n = 1, 50
+    batch = inputs.random_batch(B, n, n, n // 2, workload=inputs.WL_SWEEP, dtype=np.float32,
+                                start=16)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP, start=16)
+    sols, _ = oracle_solve_and_grad(batch, g, range(B))
+    slack = batch.h[0] - batch.G[0] @ sols[0]["z"]
+    assert np.min(np.maximum(sols[0]["lam"], slack)) < 1e-3     # the premise: nearly degenerate
+    out = _run(batch, g, np.float32)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
+
+
 @pytest.mark.parametrize("n,nineq,neq", [(60, 203, 10), (40, 180, 0), (24, 177, 7)])
 def test_global_memory_blocked_cholesky_fp32(n, nineq, neq):
     """The global-memory kernel (forced) where the Schur complement is too large for the
