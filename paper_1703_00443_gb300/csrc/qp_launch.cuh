@@ -3,6 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "qp_device.cuh"
 
 namespace qpk {
@@ -25,10 +29,28 @@ cudaError_t launch_bwd_packed_f64(const PackedBwdParams<double>& P, size_t smem,
 cudaError_t launch_bwd_f32(const BwdParams<float>& P, size_t smem, cudaStream_t st);
 cudaError_t launch_bwd_f64(const BwdParams<double>& P, size_t smem, cudaStream_t st);
 
+// Raise a kernel's dynamic shared-memory limit to at least `smem` on the current device.
+// The attribute is set once per (device, kernel, new maximum) and remembered: setting it
+// is a host-side call that can wait for work in flight, so repeating it before every
+// launch would keep launches on different streams from overlapping.
+inline cudaError_t set_smem_limit(const void* kernel, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{dev, kernel}];
+  if (have >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) have = smem;
+  return e;
+}
+
 template <typename K>
 inline cudaError_t prepare_smem(K kernel, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return set_smem_limit(reinterpret_cast<const void*>(kernel), smem);
 }
 
 }  // namespace qpk
