@@ -220,12 +220,15 @@ def serving_run(dev, rates, count):
     server = QPServer(device=dev, max_inflight=4, max_batch=512)
     runs = []
     try:
-        poisson_run(server, pool[:16], rates[0], min(64, count))       # warm-up
+        # warm-up at the highest offered rate, so batches reach their steady-state sizes and
+        # the server's pinned staging buffers their final size before anything is timed
+        poisson_run(server, pool, max(rates), min(400, count), seed=99)
         for k, rate in enumerate(rates):
             server.latencies.clear()
             server.batch_sizes.clear()
             server.completed = 0
             server.host_s = {"launch": 0.0, "retire": 0.0}
+            server.phase_s.clear()
             results, wall = poisson_run(server, pool, rate, count, seed=1 + k)
             st = server.stats()
             bad = sum(r["status"] != 0 for r in results)
@@ -233,7 +236,9 @@ def serving_run(dev, rates, count):
                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"],
                          "mean_batch": st["mean_batch"], "nonconverged": int(bad),
                          "host_ms_per_batch": st["host_launch_ms_per_batch"] +
-                         st["host_retire_ms_per_batch"]})
+                         st["host_retire_ms_per_batch"],
+                         "host_ms_by_phase": dict(st["host_launch_phases_ms_per_batch"],
+                                                  retire=st["host_retire_ms_per_batch"])})
     finally:
         server.close()
     return {"runs": runs, "max_inflight": 4,

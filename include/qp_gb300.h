@@ -204,6 +204,14 @@ int qp_forward_noalloc(const qp_options* opt, int dtype, int B, int n, int nineq
 /* Human-readable text for a QP_E* code. */
 const char* qp_strerror(int code);
 
+/* qp_host_copy_many -- host-side utility of the serving loop; the paper has no counterpart.
+ * Copies `count` host buffers: bytes[i] bytes from src[i] to dst[i], for i < count, on up to
+ * `threads` host threads (one thread for small totals).  All pointers are host memory owned
+ * by the caller; source and destination ranges must not overlap.  It touches no GPU state.
+ * Returns QP_OK, or QP_EINVAL for a negative count or null arrays. */
+int qp_host_copy_many(int count, void* const* dst, const void* const* src,
+                      const size_t* bytes, int threads);
+
 #ifdef __cplusplus
 }
 #endif

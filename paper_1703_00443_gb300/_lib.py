@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqp_gb300.so")
 
-UNITS = ["qp_abi", "qp_fwd_f32", "qp_fwd_f64", "qp_bwd", "qp_noalloc"]
+UNITS = ["qp_abi", "qp_fwd_f32", "qp_fwd_f64", "qp_bwd", "qp_noalloc", "qp_host"]
 HEADERS = ["qp_device.cuh", "qp_launch.cuh", "qp_large.cuh"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -103,6 +103,7 @@ EXPORTS = {
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                     + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 8),
     "qp_strerror": (ctypes.c_char_p, [c_int]),
+    "qp_host_copy_many": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int]),
     "qp_forward_noalloc": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                            + [c_void_p] * 12 + [c_void_p]),
     "qp_packed_plan": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,

@@ -13,8 +13,9 @@ released.  Latency is measured from each request's arrival to the resolution of 
 Each stream slot keeps one pinned host buffer for a batch's inputs and one for its results,
 grown on demand and reused: a batch is packed into sections of the input buffer with numpy
 slice copies and moves to the device in one copy, and all its results come back in one copy.
-The host copies (requests into the staging buffer, results out of it) run on a small thread
-pool: numpy releases the interpreter lock while it copies, so they proceed in parallel.
+The host copies (requests into the staging buffer, results out of it) go to the library's
+native ``qp_host_copy_many`` as one list per batch, which copies on a few host threads
+outside the interpreter lock.
 
 Each instance is solved by one thread block on the kernel path its own size selects, so a
 request's result does not depend on what it was batched with.
@@ -23,6 +24,7 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures
+import ctypes
 import dataclasses
 import threading
 import time
@@ -30,6 +32,7 @@ import time
 import numpy as np
 import torch
 
+from . import _lib
 from .packed import PackedBatch, PackedForward
 from .qp import default_options, workspace_bytes
 
@@ -43,6 +46,7 @@ class Request:
     arrival: float              # time.perf_counter() of arrival
     future: concurrent.futures.Future
     nbytes: int = 0
+    ptrs: tuple = ()            # host addresses of the six inputs and dl_dz (set by submit)
 
     @property
     def dims(self):
@@ -88,19 +92,16 @@ class Admission:
         self.reserved -= int(nbytes)
 
 
-def _balanced(tasks, parts):
-    """Split (size, payload) tasks into ``parts`` lists of about equal total size."""
-    out, load = [[] for _ in range(parts)], [0] * parts
-    for t in sorted(tasks, key=lambda t: -t[0]):
-        k = load.index(min(load))
-        out[k].append(t[1])
-        load[k] += t[0]
-    return [c for c in out if c]
-
-
-def _copy_pairs(pairs):
-    for dst, src in pairs:
-        dst[...] = src
+def _copy_many(dst, src, nbytes, threads):
+    """Host copies dst[i] <- src[i] (nbytes[i] bytes; integer addresses) in one native call."""
+    k = len(nbytes)
+    if k == 0:
+        return
+    lib = _lib.load()
+    rc = lib.qp_host_copy_many(k, (ctypes.c_void_p * k)(*dst), (ctypes.c_void_p * k)(*src),
+                               (ctypes.c_size_t * k)(*nbytes), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"qp_host_copy_many failed: {rc}")
 
 
 def _sections(sizes, align=64):
@@ -126,7 +127,8 @@ class _Staging:
     def _grow(buf, n, dtype):
         if buf.numel() >= n:
             return buf
-        return torch.empty(max(n, 2 * buf.numel()), dtype=dtype, pin_memory=True)
+        # pinned allocations are slow: leave headroom so steady-state batches reuse the buffer
+        return torch.empty(max(n + n // 4, 2 * buf.numel()), dtype=dtype, pin_memory=True)
 
     def reserve(self, n_in, n_out, n_status):
         self.inp = self._grow(self.inp, n_in, self.dtype)
@@ -144,10 +146,10 @@ class QPServer:
         self.streams = [torch.cuda.Stream(self.device) for _ in range(max_inflight)]
         import os
         self.copy_threads = int(copy_threads or min(8, os.cpu_count() or 1))
-        self.copier = concurrent.futures.ThreadPoolExecutor(self.copy_threads)
         esz = 4 if dtype == torch.float32 else 8
         self.staging = [_Staging(dtype, staging_bytes // esz) for _ in range(max_inflight)]
         self.host_s = {"launch": 0.0, "retire": 0.0}
+        self.phase_s = collections.defaultdict(float)   # host time by phase of _launch
         self.free_streams = list(range(max_inflight))
         self.admission = Admission(hbm_budget_bytes, max_batch)
         self.queue = collections.deque()
@@ -171,6 +173,7 @@ class QPServer:
         req = Request(data, np.ascontiguousarray(np.asarray(dl_dz), dtype=npdt),
                       time.perf_counter() if arrival is None else arrival, fut)
         req.nbytes = request_bytes(req.dims, self.dtype)
+        req.ptrs = tuple(x.__array_interface__["data"][0] for x in data + (req.dl_dz,))
         with self.cv:
             self.queue.append(req)
             self.cv.notify()
@@ -181,7 +184,6 @@ class QPServer:
             self._stop = True
             self.cv.notify()
         self._thread.join()
-        self.copier.shutdown()
 
     def stats(self):
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
@@ -191,7 +193,8 @@ class QPServer:
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                 "host_launch_ms_per_batch": 1e3 * self.host_s["launch"] / nb,
-                "host_retire_ms_per_batch": 1e3 * self.host_s["retire"] / nb}
+                "host_retire_ms_per_batch": 1e3 * self.host_s["retire"] / nb,
+                "host_launch_phases_ms_per_batch": {k: 1e3 * v / nb for k, v in self.phase_s.items()}}
 
     # ------------------------------------------------------------------ scheduler
     def _launch(self, reqs, sidx):
@@ -199,24 +202,31 @@ class QPServer:
         stream, stg = self.streams[sidx], self.staging[sidx]
         dims = [r.dims for r in reqs]
         keys = PackedBatch.KEYS
+        ph = self.phase_s
         with torch.cuda.stream(stream):
             pb = PackedBatch(dims, dtype=self.dtype, device=self.device, options=self.options)
+            t1 = time.perf_counter()
+            ph["plan"] += t1 - t0
             tot = pb.totals
             # inputs: Q q G h A b and dℓ/dz; results: z λ ν and the six gradients
             isec, n_in = _sections([tot[k] for k in keys] + [tot["q"]])
             osec, n_out = _sections([tot["q"], tot["h"], tot["b"]] + [tot[k] for k in keys])
             stg.reserve(n_in, n_out, len(reqs))
-            hin = stg.inp.numpy()   # gaps between instances are never read by the kernels
-            tasks = []
-            for j, key in enumerate(keys):
-                base = isec[j]
-                for o, l, r in zip(pb.offsets[key], pb.lengths[key], reqs):
-                    if l:
-                        tasks.append((int(l), (hin[base + o:base + o + l], r.data[j].reshape(-1))))
+            # gaps between instances are never read by the kernels
+            addr, esz = stg.inp.data_ptr(), stg.inp.element_size()
+            dst, src, nbytes = [], [], []
+            for j, key in enumerate(keys + ("q",)):
+                lens = pb.lengths[key]
+                keep = np.nonzero(lens)[0]
+                dst += (addr + (isec[j] + pb.offsets[key][keep]) * esz).tolist()
+                src += [reqs[i].ptrs[j] for i in keep.tolist()]   # C-contiguous (submit)
+                nbytes += (lens[keep] * esz).tolist()
+            tc = time.perf_counter()
+            ph["pack_lists"] += tc - t1
+            _copy_many(dst, src, nbytes, self.copy_threads)
             gbase = isec[len(keys)]
-            for o, l, r in zip(pb.offsets["q"], pb.lengths["q"], reqs):
-                tasks.append((int(l), (hin[gbase + o:gbase + o + l], r.dl_dz.reshape(-1))))
-            list(self.copier.map(_copy_pairs, _balanced(tasks, self.copy_threads)))
+            t2 = time.perf_counter()
+            ph["pack_copy"] += t2 - tc
             dev_in = torch.empty(n_in, dtype=self.dtype, device=self.device)
             dev_in.copy_(stg.inp[:n_in], non_blocking=True)
             view = lambda buf, off, n: buf[off:off + max(int(n), 1)]  # noqa: E731
@@ -236,7 +246,9 @@ class QPServer:
             stg.status[:len(reqs)].copy_(fo.status[:len(reqs)], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
-        self.host_s["launch"] += time.perf_counter() - t0
+        t3 = time.perf_counter()
+        ph["device"] += t3 - t2
+        self.host_s["launch"] += t3 - t0
         return {"reqs": reqs, "pb": pb, "osec": osec, "n_out": n_out, "event": ev, "stream": sidx,
                 "keep": (dev_in, dev_out, fo)}
 
@@ -247,10 +259,12 @@ class QPServer:
         n_out = item["n_out"]
         # one copy out of the staging buffer (in parallel ranges); each request's results view it
         hout = np.empty(n_out, dtype=stg.out.numpy().dtype)
-        src = stg.out[:n_out].numpy()
+        esz = hout.itemsize
         step = (n_out + self.copy_threads - 1) // self.copy_threads
-        list(self.copier.map(_copy_pairs, [[(hout[a:a + step], src[a:a + step])]
-                                           for a in range(0, n_out, step)]))
+        starts = range(0, n_out, step)
+        _copy_many([hout.ctypes.data + a * esz for a in starts],
+                   [stg.out.data_ptr() + a * esz for a in starts],
+                   [min(step, n_out - a) * esz for a in starts], self.copy_threads)
         status = stg.status.numpy()
         now = time.perf_counter()
         fields = [("z", "q", osec[0]), ("lam", "h", osec[1]), ("nu", "b", osec[2])] + \
@@ -329,8 +343,9 @@ def poisson_run(server: QPServer, pool, rate: float, count: int, seed: int = 0,
             now = time.perf_counter()
             if now >= target:
                 break
-            if target - now > 2e-4:
-                time.sleep(target - now - 1e-4)
+            # sleep, never spin: a spinning client holds the interpreter lock that the
+            # scheduler thread needs (latency still counts from the intended arrival)
+            time.sleep(min(target - now, 1e-3))
         data, g = pool[k % len(pool)]
         futs.append(server.submit(*data, g, arrival=target))
     results = [f.result(timeout=timeout) for f in futs]

@@ -74,3 +74,28 @@ def test_register_tile_capacity_includes_padding():
                 fits = tiles(nz + m + p) <= 4 * 512 and tiles(p) <= 2 * 512
                 if lib.qp_uses_global_path(0, n, p, m) == 0:
                     assert fits, (n, p, m)
+
+
+def test_host_copy_many_copies_every_range():
+    """qp_host_copy_many (the serving loop's native packing helper; host memory only)."""
+    import ctypes
+    import numpy as np
+    from paper_1703_00443_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(0)
+    srcs = [rng.standard_normal(int(k)).astype(np.float32) for k in rng.integers(0, 300000, 37)]
+    out = np.zeros(sum(len(a) for a in srcs) + 64, np.float32)
+    dst, src, nb, o = [], [], [], 0
+    for a in srcs:
+        dst.append(out.ctypes.data + 4 * o)
+        src.append(a.ctypes.data)
+        nb.append(4 * len(a))
+        o += len(a)
+    k = len(nb)
+    for threads in (1, 4):
+        out[:] = 0
+        rc = lib.qp_host_copy_many(k, (ctypes.c_void_p * k)(*dst), (ctypes.c_void_p * k)(*src),
+                                   (ctypes.c_size_t * k)(*nb), threads)
+        assert rc == 0
+        assert np.array_equal(out[:o], np.concatenate(srcs)) and not out[o:].any()
+    assert lib.qp_host_copy_many(-1, None, None, None, 1) != 0
