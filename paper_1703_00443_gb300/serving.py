@@ -2,7 +2,10 @@
 
 Requests (Q, q, G, h, A, b, ∂ℓ/∂z*) of any sizes arrive at any time.  A scheduler thread
 admits queued requests, oldest first, into a new packed batch whenever a stream slot is free
-and the HBM budget covers the batch (workspace, packed inputs, outputs and gradients).  Each
+and the HBM budget covers the batch (workspace, packed inputs, outputs and gradients).
+Requests wait in one queue per size class (by n, thresholds ``size_classes``) and a batch
+takes requests of one class, the class whose oldest request is oldest: a batch finishes
+with its largest instance, so small requests are not held back by large ones.  Each
 admitted batch runs forward and backward (one persistent launch each, ``packed.PackedBatch``)
 on its own CUDA stream, so a batch admitted while others are running overlaps with them on
 the device; its iterates and factorisation stay in device memory between the two launches.
@@ -139,7 +142,7 @@ class _Staging:
 class QPServer:
     def __init__(self, device="cuda:0", dtype=torch.float32, max_inflight=4, max_batch=1024,
                  hbm_budget_bytes=8 << 30, options=None, staging_bytes=16 << 20,
-                 copy_threads=None):
+                 copy_threads=None, size_classes=(192,)):
         self.device = torch.device(device)
         self.dtype = dtype
         self.options = options if options is not None else default_options(dtype)
@@ -152,7 +155,8 @@ class QPServer:
         self.phase_s = collections.defaultdict(float)   # host time by phase of _launch
         self.free_streams = list(range(max_inflight))
         self.admission = Admission(hbm_budget_bytes, max_batch)
-        self.queue = collections.deque()
+        self.size_classes = tuple(sorted(int(t) for t in size_classes))
+        self.queues = [collections.deque() for _ in range(len(self.size_classes) + 1)]
         self.cv = threading.Condition()
         self.inflight = []
         self.latencies = []
@@ -175,7 +179,8 @@ class QPServer:
         req.nbytes = request_bytes(req.dims, self.dtype)
         req.ptrs = tuple(x.__array_interface__["data"][0] for x in data + (req.dl_dz,))
         with self.cv:
-            self.queue.append(req)
+            n = req.dims[0]
+            self.queues[sum(n >= t for t in self.size_classes)].append(req)
             self.cv.notify()
         return fut
 
@@ -287,8 +292,10 @@ class QPServer:
             self._schedule()
         except BaseException as exc:   # fail every pending request rather than leave it waiting
             with self.cv:
-                pending = list(self.queue) + [r for item in self.inflight for r in item["reqs"]]
-                self.queue.clear()
+                pending = [r for q in self.queues for r in q] + \
+                    [r for item in self.inflight for r in item["reqs"]]
+                for q in self.queues:
+                    q.clear()
                 self.inflight = []
                 self._error = exc
             for r in pending:
@@ -300,9 +307,10 @@ class QPServer:
         torch.cuda.set_device(self.device)
         while True:
             with self.cv:
-                if self._stop and not self.queue and not self.inflight:
+                queued = any(self.queues)
+                if self._stop and not queued and not self.inflight:
                     return
-                if not self.queue and not self.inflight:
+                if not queued and not self.inflight:
                     self.cv.wait(timeout=0.05)
             progressed = False
             # retire finished batches
@@ -315,7 +323,9 @@ class QPServer:
             # admit new batches while slots and budget allow
             while self.free_streams:
                 with self.cv:
-                    reqs, rejected, _ = self.admission.take(self.queue)
+                    # the size class whose oldest request is oldest
+                    q = min((q for q in self.queues if q), key=lambda q: q[0].arrival, default=None)
+                    reqs, rejected, _ = self.admission.take(q) if q is not None else ([], [], 0)
                 for r in rejected:
                     r.future.set_exception(MemoryError(
                         f"request needs {r.nbytes} bytes, over the HBM budget {self.admission.budget}"))

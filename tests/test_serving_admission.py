@@ -47,13 +47,14 @@ def test_scheduler_failure_fails_pending_requests_instead_of_hanging():
     from paper_1703_00443_gb300.serving import QPServer, Request
 
     srv = QPServer.__new__(QPServer)
-    srv.queue = collections.deque()
+    srv.queues = [collections.deque(), collections.deque()]
     srv.inflight = []
     srv.cv = threading.Condition()
     srv._error = None
     mk = lambda: Request((), None, 0.0, concurrent.futures.Future())  # noqa: E731
     queued, running = [mk(), mk()], [mk()]
-    srv.queue.extend(queued)
+    srv.queues[0].append(queued[0])
+    srv.queues[1].append(queued[1])
     srv.inflight.append({"reqs": running})
 
     def boom():
@@ -66,7 +67,7 @@ def test_scheduler_failure_fails_pending_requests_instead_of_hanging():
         pass
     for r in queued + running:
         assert isinstance(r.future.exception(timeout=1), RuntimeError)
-    assert not srv.queue and not srv.inflight
+    assert not any(srv.queues) and not srv.inflight
     try:
         srv.submit(None, None, None, None, None, None, None)
         raise AssertionError("submit after a scheduler failure must raise")
