@@ -267,7 +267,8 @@ def run_reference(args):
         pool.join()
     tot = sum(times)
     value = per_step * args.steps / tot
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    # n_gpus: the launch this line belongs to (the oracle itself runs on rank 0's host cores)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
@@ -281,6 +282,32 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def rank_batch(rank, B, n, p, m):
+    """The batch rank `rank` solves: instances rank·B … rank·B+B−1 of the benchmark's seeded
+    stream, so ranks work on disjoint instances (weak scaling) and the union over N ranks is
+    the single-process batch of N·B instances."""
+    from paper_1703_00443_gb300 import inputs
+    batch = inputs.random_batch(B, n, p, m, workload=inputs.WL_SWEEP, dtype=np.float32,
+                                start=rank * B)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP, start=rank * B)
+    return batch, g
+
+
+def max_over_ranks(values, device, dist=None):
+    """Element-wise maximum of per-rank timings across the process group (or the values
+    themselves when there is no group)."""
+    import torch
+    t = torch.tensor(values, device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(world, per_rank_batch, ms):
+    """Solves per second of the whole job: all ranks' instances over the slowest rank's time."""
+    return world * per_rank_batch / (ms / 1e3)
+
+
 def run_gpu(args):
     import torch
 
@@ -294,9 +321,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B, n, p, m = args.batch, N_DEFAULT, NINEQ_DEFAULT, NEQ_DEFAULT
-    batch = inputs.random_batch(B, n, p, m, workload=inputs.WL_SWEEP, dtype=np.float32,
-                                start=rank * B)
-    g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP, start=rank * B)
+    batch, g = rank_batch(rank, B, n, p, m)
     host = [batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b, g]
     dev_in = [torch.from_numpy(x).to(dev) for x in host]
     Q, q, G, h, A, b, dl = dev_in
@@ -387,11 +412,9 @@ def run_gpu(args):
         packed_ms = statistics.mean(pms)
 
     # Max over ranks.
-    tvec = torch.tensor([step_ms, sum(fwd_ms) / args.steps, statistics.mean(e2e_ms)], device=dev,
-                        dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(tvec, op=dist.ReduceOp.MAX)
-    step_ms, fwd_mean, e2e_mean = tvec.tolist()
+    step_ms, fwd_mean, e2e_mean = max_over_ranks(
+        [step_ms, sum(fwd_ms) / args.steps, statistics.mean(e2e_ms)], dev,
+        dist if ws > 1 else None)
     status = st.cpu().numpy()
     iters = it.cpu().numpy()
     if rank != 0:
@@ -399,8 +422,8 @@ def run_gpu(args):
             dist.barrier()
             dist.destroy_process_group()
         return
-    value = ws * B / (step_ms / 1e3)
-    e2e_value = ws * B / (e2e_mean / 1e3)
+    value = whole_job_rate(ws, B, step_ms)
+    e2e_value = whole_job_rate(ws, B, e2e_mean)
     k_mean = float(iters.mean())
     f_fwd, f_bwd = algorithmic_flops(n, p, m, k_mean)
     achieved = f_fwd * B / (fwd_mean / 1e3) / 1e12
