@@ -346,14 +346,16 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
                                   (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
                                   status, iters, resid, (unsigned char*)workspace,
                                   o.tol, o.mu_tol, o.max_iter};
-    e = qpk::launch_fwd_packed_f32(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid, st);
+    e = qpk::launch_fwd_packed_f32(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
+                                      sizes->n_global > 0, st);
   } else {
     qpk::PackedFwdParams<double> P{B, (const qpk::PackedDesc*)desc, (int*)workspace,
                                    (const double*)Q, (const double*)q, (const double*)G,
                                    (const double*)h, (const double*)A, (const double*)b,
                                    (double*)z, (double*)lam, (double*)nu, status, iters, resid,
                                    (unsigned char*)workspace, o.tol, o.mu_tol, o.max_iter};
-    e = qpk::launch_fwd_packed_f64(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid, st);
+    e = qpk::launch_fwd_packed_f64(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
+                                      sizes->n_global > 0, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;
 }

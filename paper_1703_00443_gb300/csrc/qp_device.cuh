@@ -1478,7 +1478,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_large_kernel(const FwdPara
 // Packed batch of uneven sizes in one persistent launch: blocks take instances from an atomic
 // counter in the order of the descriptor array (largest estimated cost first), and each
 // instance runs the path its own size selects, so its result does not depend on the mix.
-template <typename T, int SW, int CH>
+// WITH_GLOBAL = false compiles the shared-memory path alone (its registers then allocated as
+// in the fixed-size kernel); the host uses it for batches without global-path instances.
+template <typename T, int SW, int CH, bool WITH_GLOBAL>
 __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const PackedFwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int s_idx;
@@ -1504,8 +1506,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const Packed
     I.resid = P.resid ? P.resid + 4 * (size_t)d.id : nullptr;
     I.ws = P.ws + d.ows;
     I.tol = P.tol; I.mu_tol = P.mu_tol; I.max_iter = P.max_iter;
-    if (d.flags & 1) fwd_global_path<T>(I, sm);
-    else fwd_smem_path<T, SW, CH>(I, sm);
+    if (d.flags & 1) {
+      if constexpr (WITH_GLOBAL) {
+        fwd_global_path<T>(I, sm);
+      } else if (threadIdx.x == 0) {
+        // Not reached (the host picks this kernel only when no instance needs the global
+        // path); should it happen, the instance is marked failed rather than run here.
+        WsLayout W;
+        W.init(I.n, I.nz, I.p, I.m, (int)sizeof(T), true);
+        reinterpret_cast<int32_t*>(I.ws + W.oSt)[0] = ST_NUM;
+        if (I.status) *I.status = ST_NUM;
+      }
+    } else {
+      fwd_smem_path<T, SW, CH>(I, sm);
+    }
     __syncthreads();
   }
 }
