@@ -23,11 +23,12 @@ def _grads_in(sizes, seed=0):
             for i, (n, p, m) in enumerate(sizes)]
 
 
-def _solve_packed(sizes, inst, gin):
-    pb = PackedBatch(sizes, device=DEV)
-    Qp, qp, Gp, hp, Ap, bp = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
+def _solve_packed(sizes, inst, gin, dtype=torch.float32):
+    npdt = np.float32 if dtype == torch.float32 else np.float64
+    pb = PackedBatch(sizes, dtype=dtype, device=DEV)
+    Qp, qp, Gp, hp, Ap, bp = pb.pack([tuple(npdt(x) for x in t) for t in inst])
     out = pb.forward(Qp, qp, Gp, hp, Ap, bp)
-    grads = pb.backward(Qp, Gp, Ap, pb.pack_vec([np.float32(g) for g in gin], "q"))
+    grads = pb.backward(Qp, Gp, Ap, pb.pack_vec([npdt(g) for g in gin], "q"))
     torch.cuda.synchronize()
     res = dict(z=pb.unpack(out.z, "q"), lam=pb.unpack(out.lam, "h"), nu=pb.unpack(out.nu, "b"),
                status=out.status[: len(sizes)].cpu().numpy())
@@ -53,6 +54,40 @@ def test_packed_equals_each_instance_alone():
         assert torch.equal(f.lam[0], res["lam"][i]), i
         for k, gg in zip(NAMES, g):
             assert torch.equal(gg[0], res[k][i]), (i, k)
+
+
+def _assert_equal_alone(inst, gin, res, npdt):
+    for i, t in enumerate(inst):
+        T = [torch.from_numpy(npdt(x)).unsqueeze(0).to(DEV) for x in t]
+        f = qp_forward(*T)
+        g = qp_backward(f, torch.from_numpy(npdt(gin[i])).unsqueeze(0).to(DEV))
+        torch.cuda.synchronize()
+        assert torch.equal(f.z[0], res["z"][i]), i
+        assert torch.equal(f.lam[0], res["lam"][i]), i
+        for k, gg in zip(NAMES, g):
+            assert torch.equal(gg[0], res[k][i]), (i, k)
+
+
+def test_packed_shared_memory_only_batch_equals_alone():
+    """A batch with no global-path instance runs the packed kernel compiled with the
+    shared-memory path alone; results stay those of each instance solved alone."""
+    sizes = [(12, 9, 2), (100, 100, 50), (7, 13, 3), (33, 40, 8), (64, 64, 16), (5, 0, 2)]
+    inst = _instances(sizes, seed=6)
+    gin = _grads_in(sizes, seed=6)
+    pb, res = _solve_packed(sizes, inst, gin)
+    assert pb.n_global == 0
+    assert (res["status"] == 0).all()
+    _assert_equal_alone(inst, gin, res, np.float32)
+
+
+def test_packed_fp64_mixed_paths_equals_alone():
+    sizes = [(10, 20, 0), (30, 150, 5), (8, 12, 3), (40, 60, 10)]
+    inst = _instances(sizes, seed=7)
+    gin = _grads_in(sizes, seed=7)
+    pb, res = _solve_packed(sizes, inst, gin, dtype=torch.float64)
+    assert pb.n_global >= 1 and pb.n_global < len(sizes)
+    assert (res["status"] == 0).all()
+    _assert_equal_alone(inst, gin, res, np.float64)
 
 
 def test_packed_uneven_sample_matches_oracle():
