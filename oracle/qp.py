@@ -158,10 +158,14 @@ def _grads(z, lam, nu, dz, dlt, dnu):
     )
 
 
-def backward(Q, G, h, A, sol, dl_dz):
+def backward(Q, G, h, A, sol, dl_dz, dl_dlam=None, dl_dnu=None):
     """Adjoint solve of Eq. 7 at the solution and gradients of Eq. 8.
 
-    [d_z; d_λ; d_ν] = −[[Q, GᵀD(λ*), Aᵀ], [G, D(Gz*−h), 0], [A, 0, 0]]⁻¹ [(∂ℓ/∂z*)ᵀ; 0; 0].
+    [d_z; d_λ; d_ν] = −[[Q, GᵀD(λ*), Aᵀ], [G, D(Gz*−h), 0], [A, 0, 0]]⁻¹
+                       [(∂ℓ/∂z*)ᵀ; (∂ℓ/∂λ*)ᵀ; (∂ℓ/∂ν*)ᵀ].
+    Eq. 7 as printed has zeros in the last two blocks (the paper does not differentiate
+    through λ*, ν*); a loss that depends on them puts its derivatives there (chain rule
+    through the same implicit differentiation of Eq. 6), and Eq. 8 is unchanged.
     Returns the six gradients plus d_z, d_λ, d̃_λ = D(λ*)d_λ and d_ν.
     """
     Q, G, h, A = (np.asarray(x, dtype=np.float64) for x in (Q, G, h, A))
@@ -175,7 +179,9 @@ def backward(Q, G, h, A, sol, dl_dz):
     K[n:n + p, :n] = G
     K[n:n + p, n:n + p] = np.diag(G @ z - h)
     K[n + p:, :n] = A
-    rhs = np.concatenate([np.asarray(dl_dz, dtype=np.float64), np.zeros(p + m)])
+    gl = np.zeros(p) if dl_dlam is None else np.asarray(dl_dlam, dtype=np.float64)
+    gn = np.zeros(m) if dl_dnu is None else np.asarray(dl_dnu, dtype=np.float64)
+    rhs = np.concatenate([np.asarray(dl_dz, dtype=np.float64), gl, gn])
     d = -np.linalg.solve(K, rhs)
     dz, dl, dnu = d[:n], d[n:n + p], d[n + p:]
     dlt = lam * dl
@@ -184,16 +190,19 @@ def backward(Q, G, h, A, sol, dl_dz):
     return out
 
 
-def backward_sym(Q, G, A, sol, dl_dz):
+def backward_sym(Q, G, A, sol, dl_dz, dl_dlam=None, dl_dnu=None):
     """The same adjoint through the symmetrised KKT matrix of §3.1.1, Eq. 11:
-    K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z*; 0; 0; 0], K_sym = K of Eq. 9 with its second
-    block row scaled by D(1/s)."""
+    K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z*; 0; −∂ℓ/∂λ*; −∂ℓ/∂ν*], K_sym = K of Eq. 9 with
+    its second block row scaled by D(1/s).  (Eliminating d_s from rows 2 and 3 gives
+    G d_z − D(s/λ) d̃_λ = −∂ℓ/∂λ*, which is the λ row of Eq. 7 written in d̃_λ = D(λ*) d_λ.)"""
     Q, G, A = (np.asarray(x, dtype=np.float64) for x in (Q, G, A))
     z, s, lam, nu = sol["z"], sol["s"], sol["lam"], sol["nu"]
     n, p, m = Q.shape[0], G.shape[0], A.shape[0]
     K = kkt_matrix(Q, G, A, s, lam)
     K[n:n + p, :] /= s[:, None]
-    rhs = np.concatenate([-np.asarray(dl_dz, dtype=np.float64), np.zeros(2 * p + m)])
+    gl = np.zeros(p) if dl_dlam is None else np.asarray(dl_dlam, dtype=np.float64)
+    gn = np.zeros(m) if dl_dnu is None else np.asarray(dl_dnu, dtype=np.float64)
+    rhs = np.concatenate([-np.asarray(dl_dz, dtype=np.float64), np.zeros(p), -gl, -gn])
     dz, ds, dlt, dnu = _split(np.linalg.solve(K, rhs), n, p, m)
     out = _grads(z, lam, nu, dz, dlt, dnu)
     out.update(d_z=dz, d_s=ds, d_lam_tilde=dlt, d_nu=dnu)

@@ -325,6 +325,54 @@ def test_central_finite_differences():
             assert abs(fd - adj) <= 1e-6 * (1 + abs(adj)), (name, idx, fd, adj)
 
 
+def test_central_finite_differences_through_lambda_and_nu():
+    """ℓ = g_zᵀz* + g_λᵀλ* + g_νᵀν*: the adjoint with all three right-hand-side blocks matches
+    central differences of the oracle's solution (strictly complementary instance)."""
+    r = _rng(301)
+    n, p, m = 5, 7, 2
+    Q, q, G, h, A, b = _tiny_qp(r, n, p, m)
+    q = 2.0 * q
+    gz, gl, gn = r.standard_normal(n), r.standard_normal(p), r.standard_normal(m)
+    sol = oracle.solve(Q, q, G, h, A, b)
+    slack = h - G @ sol["z"]
+    assert np.min(np.maximum(sol["lam"], slack)) > 1e-3     # strict complementarity
+    gr = oracle.backward(Q, G, h, A, sol, gz, gl, gn)
+    params = dict(Q=Q, q=q, G=G, h=h, A=A, b=b)
+
+    def loss(pp):
+        s2 = oracle.solve(pp["Q"], pp["q"], pp["G"], pp["h"], pp["A"], pp["b"])
+        return gz @ s2["z"] + gl @ s2["lam"] + gn @ s2["nu"]
+
+    for name, val in params.items():
+        for idx in list(np.ndindex(*val.shape))[::2]:
+            eps = 1e-6 * max(1.0, abs(val[idx]))
+            plus = {kk: v.copy() for kk, v in params.items()}
+            minus = {kk: v.copy() for kk, v in params.items()}
+            plus[name][idx] += eps
+            minus[name][idx] -= eps
+            sym = name == "Q" and idx[0] != idx[1]
+            if sym:
+                plus[name][idx[::-1]] += eps
+                minus[name][idx[::-1]] -= eps
+            fd = (loss(plus) - loss(minus)) / (2 * eps)
+            adj = gr["d" + name][idx]
+            if sym:
+                adj = adj + gr["d" + name][idx[::-1]]
+            assert abs(fd - adj) <= 1e-6 * (1 + abs(adj)), (name, idx, fd, adj)
+
+
+@pytest.mark.parametrize("n,p,m", [(10, 20, 3), (6, 11, 2)])
+def test_two_adjoint_derivations_agree_with_lambda_and_nu_terms(n, p, m):
+    Q, q, G, h, A, b = inputs.random_qp(n, p, m, index=4)
+    sol = oracle.solve(Q, q, G, h, A, b)
+    r = _rng(302)
+    gz, gl, gn = r.standard_normal(n), r.standard_normal(p), r.standard_normal(m)
+    g1 = oracle.backward(Q, G, h, A, sol, gz, gl, gn)
+    g2 = oracle.backward_sym(Q, G, A, sol, gz, gl, gn)
+    for key in ("dQ", "dq", "dG", "dh", "dA", "db"):
+        np.testing.assert_allclose(g1[key], g2[key], rtol=1e-7, atol=1e-9, err_msg=key)
+
+
 @pytest.mark.parametrize("n,p,m", [(10, 20, 0), (20, 20, 10), (4, 9, 1)])
 def test_two_adjoint_derivations_agree(n, p, m):
     """Eq. 7 (transposed Eq. 6 matrix) and Eq. 11 (symmetrised K) give the same d_z, d̃_λ,
