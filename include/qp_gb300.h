@@ -121,6 +121,25 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                 void* dQ, void* dq, void* dG, void* dh, void* dA, void* db, void* stream);
 
 /*
+ * qp_backward_ext -- qp_backward for a loss that also depends on λ* and ν*.
+ *
+ * §3 differentiates z* only (it sets the λ*, ν* case aside).  The same implicit
+ * differentiation of Eq. 6 gives, for a loss of (z*, λ*, ν*), the adjoint of Eq. 7 with
+ * right-hand side [∂ℓ/∂z*; ∂ℓ/∂λ*; ∂ℓ/∂ν*] instead of [∂ℓ/∂z*; 0; 0], and the gradients of
+ * Eq. 8 unchanged.  In the symmetrised form of Eq. 11 the two new blocks enter the primal
+ * feasibility rows: K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z*; 0; −∂ℓ/∂λ*; −∂ℓ/∂ν*].
+ *
+ * dl_dlam: [B, nineq] and dl_dnu: [B, neq], device memory of the dtype, row-major; either
+ * may be null (zero).  dl_dz is required (pass zeros for a loss of λ*, ν* alone).  All other
+ * arguments, outputs and errors as qp_backward; qp_backward(...) is this call with both null.
+ */
+int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+                    const void* Q, const void* G, const void* A,
+                    const void* workspace, size_t workspace_bytes, const void* dl_dz,
+                    const void* dl_dlam, const void* dl_dnu,
+                    void* dQ, void* dq, void* dG, void* dh, void* dA, void* db, void* stream);
+
+/*
  * Packed batches of uneven sizes (one persistent launch each way).
  *
  * Instance i has its own (n_i, nineq_i, neq_i); its data are packed back to back in index

@@ -102,6 +102,8 @@ EXPORTS = {
                    + [c_void_p] * 13 + [c_size_t, c_void_p]),
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                     + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 8),
+    "qp_backward_ext": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
+                        + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 10),
     "qp_strerror": (ctypes.c_char_p, [c_int]),
     "qp_host_copy_many": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int]),
     "qp_forward_noalloc": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]

@@ -1,8 +1,9 @@
 """``QPFunction``: the OptNet QP layer as a ``torch.autograd.Function`` (§3).
 
-forward(Q, q, G, h, A, b) -> z* (λ* and ν* are returned too, marked non-differentiable:
-the paper forms Jacobians of z* only).  backward(∂ℓ/∂z*) -> the six parameter gradients of
-Eq. 8, from the factorisation the forward pass left in its workspace (§3.1.1).
+forward(Q, q, G, h, A, b) -> z*, λ*, ν*, status.  backward(∂ℓ/∂z*, ∂ℓ/∂λ*, ∂ℓ/∂ν*) -> the
+six parameter gradients of Eq. 8, from the factorisation the forward pass left in its
+workspace (§3.1.1).  The paper differentiates z* only; λ* and ν* are differentiable here
+through the same adjoint with the extra right-hand-side blocks (``qp_backward_ext``).
 """
 from __future__ import annotations
 
@@ -17,15 +18,19 @@ class QPFunction(torch.autograd.Function):
         fwd = qp_forward(Q, q, G, h, A, b, options=options)
         ctx.fwd = fwd
         ctx.shapes = (G is None, A is None)
-        ctx.mark_non_differentiable(fwd.lam, fwd.nu)
+        ctx.mark_non_differentiable(fwd.status)
+        ctx.set_materialize_grads(False)   # unused outputs' gradients arrive as None
         return fwd.z, fwd.lam, fwd.nu, fwd.status
 
     @staticmethod
     def backward(ctx, dz, dlam, dnu, dstatus):
-        if dz is None:
+        if dz is None and dlam is None and dnu is None:
             return (None,) * 7
+        if dz is None:
+            dz = torch.zeros_like(ctx.fwd.z)
         need = ctx.needs_input_grad[:6]
-        g = qp_backward(ctx.fwd, dz, need=tuple(bool(x) for x in need))
+        g = qp_backward(ctx.fwd, dz, dl_dlam=dlam, dl_dnu=dnu,
+                        need=tuple(bool(x) for x in need))
         no_g, no_a = ctx.shapes
         grads = list(g)
         if no_g:

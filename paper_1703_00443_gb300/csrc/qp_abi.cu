@@ -222,6 +222,15 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                 const void* Q, const void* G, const void* A, const void* workspace,
                 size_t workspace_bytes, const void* dl_dz, void* dQ, void* dq, void* dG,
                 void* dh, void* dA, void* db, void* stream) {
+  return qp_backward_ext(opt, dtype, B, n, nineq, neq, Q, G, A, workspace, workspace_bytes,
+                         dl_dz, nullptr, nullptr, dQ, dq, dG, dh, dA, db, stream);
+}
+
+int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
+                    const void* Q, const void* G, const void* A, const void* workspace,
+                    size_t workspace_bytes, const void* dl_dz, const void* dl_dlam,
+                    const void* dl_dnu, void* dQ, void* dq, void* dG, void* dh, void* dA,
+                    void* db, void* stream) {
   if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return QP_EINVAL;
   if (B == 0) return QP_OK;
   if (!Q || !dl_dz || !workspace) return QP_EINVAL;
@@ -242,14 +251,15 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                             (const float*)Q, (const float*)G, (const float*)A,
                             (const float*)dl_dz, (float*)dQ, (float*)dq, (float*)dG, (float*)dh,
                             (float*)dA, (float*)db, (const unsigned char*)workspace,
-                            pl.ws, o.refine};
+                            pl.ws, o.refine, (const float*)dl_dlam, (const float*)dl_dnu};
     e = qpk::launch_bwd_f32(P, smem, st);
   } else {
     qpk::BwdParams<double> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0,
                              (const double*)Q, (const double*)G,
                              (const double*)A, (const double*)dl_dz, (double*)dQ, (double*)dq,
                              (double*)dG, (double*)dh, (double*)dA, (double*)db,
-                             (const unsigned char*)workspace, pl.ws, o.refine};
+                             (const unsigned char*)workspace, pl.ws, o.refine,
+                             (const double*)dl_dlam, (const double*)dl_dnu};
     e = qpk::launch_bwd_f64(P, smem, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;

@@ -215,6 +215,7 @@ struct BwdInst {
   T *dQ, *dq, *dG, *dh, *dA, *db;
   const unsigned char* ws;
   int refine;
+  const T *dl_dlam, *dl_dnu;   // ∂ℓ/∂λ*, ∂ℓ/∂ν* of this instance (or null: zero)
 };
 
 // Descriptor of one instance of a packed (uneven) batch; the C ABI's qp_instance_desc has
@@ -258,6 +259,7 @@ struct BwdParams {
   const unsigned char* ws;
   size_t ws_inst;
   int refine;
+  const T *dl_dlam, *dl_dnu;   // [B, nineq], [B, neq] or null (zero)
 };
 
 // ------------------------------------------------------------------ FP64-accurate dot products
@@ -1554,6 +1556,8 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   const T* Gb = p ? P.G : nullptr;
   const T* Ab = m ? P.A : nullptr;
   const T* gz = P.dl_dz;
+  const T* gl = P.dl_dlam;   // may be null: zero
+  const T* gn = P.dl_dnu;    // may be null: zero
 
   if (status == ST_NOTPD || status == ST_NUM) {
     const T qn = (T)__longlong_as_double(0x7ff8000000000000LL);
@@ -1566,17 +1570,26 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     return;
   }
   for (int i = tid; i < n + 2 * p + m; i += NTHREADS) dv[i] = wIt[i];
-  for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? -gz[i] : T(0);
+  for (int i = tid; i < m1; i += NTHREADS)
+    u[i] = (i < n) ? -gz[i] : ((i >= nz && gn) ? -gn[i - nz] : T(0));
   __syncthreads();
 
-  // K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z; 0; 0; 0]  (Eq. 11), reduced form.
+  // K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z; 0; −∂ℓ/∂λ; −∂ℓ/∂ν]  (Eq. 11; the last two blocks
+  // are zero for a loss of z* alone), reduced form:
+  //   (M + D(s/λ)) d̃_λ = RE·u + ∂ℓ/∂λ,  [d_z; d_ν] = S·u − REᵀ d̃_λ,  u = [−∂ℓ/∂z; −∂ℓ/∂ν].
   mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
   __syncthreads();
+  const T* rhs0 = wv + m1;
+  if (gl) {
+    for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] + gl[i];
+    __syncthreads();
+    rhs0 = rhs;
+  }
   // The global-memory path leaves a blocked factor instead of X for large p.
   const bool blk = P.large && !reg_chol_ok(p, (int)sizeof(T));
   if (p > 0) {
-    if (blk) blk_solve(p, X, p, wv + m1, y, dl, tscr);
-    else chol_solve(p, X, p, wv + m1, y, dl, tscr);
+    if (blk) blk_solve(p, X, p, rhs0, y, dl, tscr);
+    else chol_solve(p, X, p, rhs0, y, dl, tscr);
   }
   mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
           [&](int c, T val) { dzn[c] = wv[c] - val; });
@@ -1600,15 +1613,18 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)gz[i]));
+    if (gl) for (int i = tid; i < p; i += NTHREADS) v[1] = fmaxf(v[1], fabsf((float)gl[i]));
+    if (gn) for (int i = tid; i < m; i += NTHREADS) v[2] = fmaxf(v[2], fabsf((float)gn[i]));
     block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
-    gfloor = 1e-3f * v[0];
+    gfloor = 1e-3f * fmaxf(v[0], fmaxf(v[1], v[2]));
   }
   for (int rs = 0; rs < P.refine; ++rs) {
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
     __syncthreads();
     kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, 4 * NTHREADS, [&](int j) { return (double)gz[j]; },
-                 [&](int i) { return -(s[i] / lam[i]) * dlt[i]; }, [&](int) { return 0.0; },
+                 [&](int i) { return -(s[i] / lam[i]) * dlt[i] + (gl ? (double)gl[i] : 0.0); },
+                 [&](int i) { return gn ? (double)gn[i] : 0.0; },
                  rz, rl, rn);
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
     __syncthreads();
@@ -1706,6 +1722,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   I.db = P.db ? P.db + (size_t)bi * m : nullptr;
   I.ws = P.ws + (size_t)bi * P.ws_inst;
   I.refine = P.refine;
+  I.dl_dlam = P.dl_dlam ? P.dl_dlam + (size_t)bi * p : nullptr;
+  I.dl_dnu = P.dl_dnu ? P.dl_dnu + (size_t)bi * m : nullptr;
   bwd_body<T>(I, sm);
 }
 
@@ -1735,6 +1753,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_packed_kernel(const Packed
     I.db = P.db ? P.db + d.ob : nullptr;
     I.ws = P.ws + d.ows;
     I.refine = P.refine;
+    I.dl_dlam = nullptr;   // the packed entry takes ∂ℓ/∂z* only
+    I.dl_dnu = nullptr;
     bwd_body<T>(I, sm);
     __syncthreads();
   }

@@ -150,10 +150,11 @@ def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=
     return ForwardResult(z, lam, nu, status, iters, resid, workspace, Q, G, A, opts)
 
 
-def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, need=(True,) * 6, options=None,
-                out=None):
-    """Gradients (dQ, dq, dG, dh, dA, db) of ℓ(z*) (C ABI ``qp_backward``); entries for which
-    ``need`` is False come back as None."""
+def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, dl_dlam=None, dl_dnu=None,
+                need=(True,) * 6, options=None, out=None):
+    """Gradients (dQ, dq, dG, dh, dA, db) of ℓ(z*) (C ABI ``qp_backward``), or of ℓ(z*, λ*, ν*)
+    when ``dl_dlam`` ([B, nineq]) or ``dl_dnu`` ([B, neq]) is given (``qp_backward_ext``);
+    entries for which ``need`` is False come back as None."""
     Q, G, A = fwd.Q, fwd.G, fwd.A
     B, n, nineq, neq = Q.shape[0], Q.shape[1], G.shape[1], A.shape[1]
     dev, dt = Q.device, Q.dtype
@@ -167,9 +168,24 @@ def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, need=(True,) * 6, op
         grads = [torch.empty(s, device=dev, dtype=dt) if w else None for s, w in zip(shapes, need)]
     else:
         grads = list(out)
+    extra = []
+    for name, t, k in (("dl_dlam", dl_dlam, nineq), ("dl_dnu", dl_dnu, neq)):
+        if t is not None:
+            t = t.to(device=dev, dtype=dt).contiguous()
+            if tuple(t.shape) != (B, k):
+                raise QPError(f"{name} has shape {tuple(t.shape)}, expected {(B, k)}")
+        extra.append(t if t is not None and t.numel() else None)
     with torch.cuda.device(dev):
-        rc = lib.qp_backward(ctypes.byref(opts), _dtype_code(Q), B, n, nineq, neq,
-                             _ptr(Q), _ptr(G), _ptr(A), _ptr(fwd.workspace), fwd.workspace.numel(),
-                             _ptr(dl_dz), *[_ptr(g) for g in grads], _stream_handle(dev))
+        if extra[0] is None and extra[1] is None:
+            rc = lib.qp_backward(ctypes.byref(opts), _dtype_code(Q), B, n, nineq, neq,
+                                 _ptr(Q), _ptr(G), _ptr(A), _ptr(fwd.workspace),
+                                 fwd.workspace.numel(), _ptr(dl_dz),
+                                 *[_ptr(g) for g in grads], _stream_handle(dev))
+        else:
+            rc = lib.qp_backward_ext(ctypes.byref(opts), _dtype_code(Q), B, n, nineq, neq,
+                                     _ptr(Q), _ptr(G), _ptr(A), _ptr(fwd.workspace),
+                                     fwd.workspace.numel(), _ptr(dl_dz), _ptr(extra[0]),
+                                     _ptr(extra[1]), *[_ptr(g) for g in grads],
+                                     _stream_handle(dev))
     _check(rc)
     return tuple(grads)

@@ -56,3 +56,22 @@ def test_no_constraint_tensors_give_none_grads():
     ref = -torch.linalg.solve(Q.detach().double(), q.detach().double().unsqueeze(-1)).squeeze(-1)
     assert torch.allclose(z.double(), ref, rtol=1e-5, atol=1e-6)
     assert q.grad is not None and Q.grad is not None
+
+
+def test_gradcheck_fp64_through_lambda_and_nu():
+    """λ* and ν* as differentiable outputs (the adjoint's extra right-hand-side blocks):
+    gradcheck against central differences of the FP64 solve."""
+    from paper_1703_00443_gb300.autograd import QPFunction
+    n, p, m = 4, 6, 1
+    batch = inputs.random_batch(2, n, p, m, workload=inputs.WL_PLAIN, dtype=np.float64, start=77)
+    Q, q, G, h, A, b = (torch.from_numpy(x).to(DEV) for x in
+                        (batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b))
+    q = (2.0 * q).requires_grad_(True)
+    h.requires_grad_(True)
+    b.requires_grad_(True)
+
+    def f(q_, h_, b_):
+        z, lam, nu, _ = QPFunction.apply(Q, q_, G, h_, A, b_)
+        return z, lam, nu
+
+    assert torch.autograd.gradcheck(f, (q, h, b), eps=1e-6, atol=1e-6, rtol=1e-5)

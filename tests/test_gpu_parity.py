@@ -183,6 +183,46 @@ def test_global_memory_kernel_small_sizes(n, nineq, neq):
     _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
 
 
+@pytest.mark.parametrize("dtype,path,n,nineq,neq", [(np.float32, 0, 20, 30, 5),
+                                                    (np.float32, 1, 16, 181, 4),
+                                                    (np.float64, 0, 10, 20, 3)])
+def test_gradients_through_lambda_and_nu(dtype, path, n, nineq, neq):
+    """ℓ = g_zᵀz* + g_λᵀλ* + g_νᵀν* through qp_backward_ext: the adjoint with the extra
+    right-hand-side blocks, against the oracle (shared-memory path, the global path's blocked
+    factor, FP64)."""
+    from paper_1703_00443_gb300 import default_options
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    opts = default_options(tdt)
+    opts.path = path
+    B = 3
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_PLAIN, dtype=dtype, start=900)
+    r = np.random.default_rng(9)
+    gz = r.standard_normal((B, n)).astype(dtype)
+    gl = r.standard_normal((B, nineq)).astype(dtype)
+    gn = r.standard_normal((B, neq)).astype(dtype)
+    T = _to_dev(batch, dtype)
+    fwd = qp_forward(*T, options=opts)
+    grads = qp_backward(fwd, torch.from_numpy(gz).to(DEV), dl_dlam=torch.from_numpy(gl).to(DEV),
+                        dl_dnu=torch.from_numpy(gn).to(DEV))
+    torch.cuda.synchronize()
+    assert (fwd.status == 0).all()
+    import oracle
+    tol = 1e-4 if dtype == np.float32 else 1e-8
+    for i in range(B):
+        Q, q, G, h, A, b = batch.instance(i)
+        sol = oracle.solve(Q, q, G, h, A, b)
+        ref = oracle.backward(Q, G, h, A, sol, gz[i].astype(np.float64), gl[i].astype(np.float64),
+                              gn[i].astype(np.float64))
+        scale = np.linalg.norm(np.concatenate([gz[i], gl[i], gn[i]]).astype(np.float64))
+        for k, t in zip(GRAD_NAMES, grads):
+            got = t[i].double().cpu().numpy()
+            if ref[k].size == 0:
+                continue
+            fl = 1e-3 * scale * (max(1.0, np.linalg.norm(sol["z"])) if k in ("dQ", "dG", "dA") else 1.0)
+            e = np.linalg.norm(got - ref[k]) / max(np.linalg.norm(ref[k]), fl)
+            assert e <= tol, (i, k, e)
+
+
 def test_nearly_degenerate_instance_gradients_fp32():
     """An instance of the n = 50 timing sweep whose most weakly resolved constraint has
     max(λ_i, s_i) ≈ 5e-4 at the solution.  Its gradient is sensitive to how far the final
