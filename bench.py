@@ -98,7 +98,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(HERE, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples (the JSON line carries their summary); BENCH_CLOCKS_DIR keeps them
+        import tempfile
+        self.path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"qp_bench_clocks_rank{index}.csv")
 
     def start(self):
         try:
