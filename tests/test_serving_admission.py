@@ -73,3 +73,37 @@ def test_scheduler_failure_fails_pending_requests_instead_of_hanging():
         raise AssertionError("submit after a scheduler failure must raise")
     except RuntimeError:
         pass
+
+
+def test_submit_routes_requests_by_size_class():
+    """submit() queues a request in the class of its n (thresholds size_classes) and records
+    its host addresses once (host logic only, no GPU)."""
+    import collections
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1703_00443_gb300.serving import QPServer
+
+    srv = QPServer.__new__(QPServer)
+    srv.dtype = torch.float32
+    srv.size_classes = (32, 192)
+    srv.queues = [collections.deque() for _ in range(3)]
+    srv.cv = threading.Condition()
+    srv._error = None
+    for n in (8, 31, 32, 100, 192, 300):
+        data = (np.eye(n), np.zeros(n), np.ones((n, n)), np.ones(n), np.zeros((0, n)), np.zeros(0))
+        srv.submit(*data, np.zeros(n))
+    assert [[r.dims[0] for r in q] for q in srv.queues] == [[8, 31], [32, 100], [192, 300]]
+    r = srv.queues[2][1]
+    assert len(r.ptrs) == 7 and r.ptrs[0] == r.data[0].__array_interface__["data"][0]
+    assert all(x.dtype == np.float32 and x.flags.c_contiguous for x in r.data)
+
+
+def test_sections_are_aligned_and_disjoint():
+    from paper_1703_00443_gb300.serving import _sections
+    offs, total = _sections([0, 5, 64, 65, 1])
+    assert all(o % 64 == 0 for o in offs)
+    ends = [o + max(k, 1) for o, k in zip(offs, [0, 5, 64, 65, 1])]
+    assert all(e <= nxt for e, nxt in zip(ends, offs[1:] + [total]))
