@@ -15,7 +15,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -314,7 +313,7 @@ def whole_job_rate(world, per_rank_batch, ms):
 def run_gpu(args):
     import torch
 
-    from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward
+    from paper_1703_00443_gb300 import qp_backward, qp_forward
     from paper_1703_00443_gb300.qp import alloc_workspace
 
     ws, rank, local = _dist()
