@@ -192,7 +192,9 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
                       void* workspace, size_t workspace_bytes, void* stream);
 
 /* Backward pass of a packed batch, after qp_forward_packed with the same desc, sizes and
- * workspace.  dl_dz is packed like z; the gradients like the inputs. */
+ * workspace.  dl_dz is packed like z; the gradients like the inputs.  It differentiates a
+ * loss of z* (for a loss that also depends on λ*, ν*, use qp_backward_ext on a fixed-size
+ * batch). */
 int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
                        const qp_packed_sizes* sizes, const void* Q, const void* G,
                        const void* A, const void* workspace, size_t workspace_bytes,
