@@ -29,7 +29,12 @@ sys.path.insert(0, HERE)
 B_DEFAULT, N_DEFAULT, NINEQ_DEFAULT, NEQ_DEFAULT = 128, 100, 100, 50
 METRIC = "QP fwd+bwd solves/sec (n=100, batch 128) @ rel err ≤1e-5; p50/p99 latency served"
 UNIT = "solves/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs × FP32 lanes × 2 flop/FMA × max clock
+SM_MAX_MHZ = 2070.0   # GB300 maximum SM clock
+
+
+def fp32_peak_tflops(sms, mhz=SM_MAX_MHZ):
+    """FP32 FMA roofline: SMs × 128 FP32 lanes × 2 flop per FMA × clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def algorithmic_flops(n, p, m, iters):
@@ -142,8 +147,12 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle legs
+RESULTS = ("z", "lam", "nu", "dQ", "dq", "dG", "dh", "dA", "db")
+
+
 def _oracle_instance(args):
-    """Forward + backward of one instance with the FP64 oracle (runs in a worker process)."""
+    """Forward + backward of one instance with the FP64 oracle (runs in a worker process);
+    returns its index, the time taken and every result."""
     n, p, m, idx = args
     import oracle
     from paper_1703_00443_gb300 import inputs
@@ -154,7 +163,9 @@ def _oracle_instance(args):
     sol = oracle.solve(Q, q, G, h, A, b)
     gr = oracle.backward(Q, G, h, A, sol, g)
     dt = time.perf_counter() - t0
-    return idx, dt, sol["z"], gr["dq"], gr["dG"], gr["dQ"]
+    res = {k: sol[k] for k in ("z", "lam", "nu")}
+    res.update({k: gr[k] for k in ("dQ", "dq", "dG", "dh", "dA", "db")})
+    return idx, dt, res, g
 
 
 def _oracle_pool(workers):
@@ -172,10 +183,38 @@ def _oracle_pool(workers):
     return pool
 
 
+def accuracy_vs_oracle(gpu_out, done):
+    """Worst error of every GPU result against the FP64 oracle over the given instances, in
+    the two forms of the relative error: ‖x − x_ref‖₂/max(‖x_ref‖₂, floor) and
+    max_i |x_i − x_ref,i|/max(‖x_ref‖∞, floor).  floor = 1e-12 for z*, λ*, ν*; for a
+    gradient 1e-3·‖∂ℓ/∂z*‖ (times max(1, ‖z*‖) for dQ, dG, dA), because a gradient can vanish
+    identically at the solution (e.g. dq at a vertex)."""
+    worst = {}
+    for idx, _, ref, g in done:
+        for k in RESULTS:
+            r = np.asarray(ref[k], dtype=np.float64).ravel()
+            x = np.asarray(gpu_out[k][idx], dtype=np.float64).ravel()
+            if r.size == 0:
+                continue
+            for form, ordv in (("l2", None), ("inf", np.inf)):
+                fl = 1e-12
+                if k.startswith("d"):
+                    fl = 1e-3 * np.linalg.norm(g, ord=ordv)
+                    if k in ("dQ", "dG", "dA"):
+                        fl *= max(1.0, np.linalg.norm(ref["z"], ord=ordv))
+                e = np.linalg.norm(x - r, ord=ordv) / max(np.linalg.norm(r, ord=ordv), fl)
+                key = f"{k}_{form}"
+                worst[key] = max(worst.get(key, 0.0), float(e))
+    return {"instances": len(done), "rel_err_max": worst,
+            "bar": {"z": 1e-5, "gradients": 1e-4, "lam_nu": 1e-4},
+            "within_bar": all(v <= (1e-5 if k.startswith("z_") else 1e-4)
+                              for k, v in worst.items())}
+
+
 def cpu_baseline(n, p, m, budget_s=15.0, gpu_out=None):
     """The oracle as it stands, one instance per process (BLAS threads = 1), all host cores,
-    on a bounded sample of the same instances; also returns its results for an accuracy
-    check of the GPU outputs on that sample."""
+    on a bounded sample of the same instances (timed), and on one core; then, untimed, the
+    rest of the batch so that every GPU result of the step is checked against FP64."""
     cores = os.cpu_count() or 1
     pool = _oracle_pool(cores)
     try:
@@ -188,22 +227,27 @@ def cpu_baseline(n, p, m, budget_s=15.0, gpu_out=None):
             done += pool.map(_oracle_instance, [(n, p, m, i) for i in idxs if i < B_DEFAULT])
             batch_idx += 1
         wall = time.perf_counter() - t0
+        timed = len(done)
+        if gpu_out is not None:
+            have = {d[0] for d in done}
+            done += pool.map(_oracle_instance, [(n, p, m, i) for i in range(B_DEFAULT)
+                                                if i not in have])
     finally:
         pool.close()
         pool.join()
-    res = {"value": len(done) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{len(done)} of the {B_DEFAULT} step instances (n={n}, nineq={p}, neq={m}), "
-                     f"FP64 dense-KKT PDIPM fwd+bwd, one instance per process, BLAS threads 1"}
-    acc = None
-    if gpu_out is not None and done:
-        ez, eg = [], []
-        for idx, _, z, dq, dG, dQ in done:
-            def rel(a, r):
-                return float(np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-12))
-            ez.append(rel(gpu_out["z"][idx], z))
-            eg.append(max(rel(gpu_out["dq"][idx], dq), rel(gpu_out["dG"][idx], dG),
-                          rel(gpu_out["dQ"][idx], dQ)))
-        acc = {"instances": len(done), "z_rel_err_max": max(ez), "grad_rel_err_max": max(eg)}
+    # one core, in this process: a few instances
+    t1 = time.perf_counter()
+    k1 = 0
+    while k1 < 8 and (k1 == 0 or time.perf_counter() - t1 < budget_s / 3):
+        _oracle_instance((n, p, m, k1))
+        k1 += 1
+    one = k1 / (time.perf_counter() - t1)
+    res = {"value": timed / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{timed} of the {B_DEFAULT} step instances (n={n}, nineq={p}, neq={m}), "
+                     f"FP64 dense-KKT PDIPM fwd+bwd, one instance per process, BLAS threads 1",
+           "one_core": {"value": one, "unit": UNIT, "cores": 1,
+                        "sample": f"{k1} instances in one process"}}
+    acc = accuracy_vs_oracle(gpu_out, done) if gpu_out is not None and done else None
     return res, acc
 
 
@@ -429,8 +473,14 @@ def run_gpu(args):
     k_mean = float(iters.mean())
     f_fwd, f_bwd = algorithmic_flops(n, p, m, k_mean)
     achieved = f_fwd * B / (fwd_mean / 1e3) / 1e12
-    gpu_out = {"z": z.cpu().numpy(), "dq": gout[1].cpu().numpy(), "dG": gout[2].cpu().numpy(),
-               "dQ": gout[0].cpu().numpy()}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sms)
+    gpu_out = {"z": z.cpu().numpy(), "lam": lam.cpu().numpy(), "nu": nu.cpu().numpy()}
+    gpu_out.update({k: t.cpu().numpy() for k, t in zip(("dQ", "dq", "dG", "dh", "dA", "db"), gout)})
+    # backward status words of the step (flag bits mark nearly degenerate solutions)
+    bstat = torch.empty((B,), device=dev, dtype=torch.int32)
+    qp_backward(fwd, dl, out=[torch.empty_like(t) for t in gout], status=bstat)
+    bstat = bstat.cpu().numpy()
     served = None
     if not args.no_extras and ws == 1:
         served = serving_run(dev, [float(r) for r in str(args.serve_rate).split(",")],
@@ -451,10 +501,13 @@ def run_gpu(args):
                    "fwd_ms": fwd_mean, "bwd_ms": step_ms - fwd_mean,
                    "iters_mean": k_mean, "iters_max": int(iters.max()),
                    "status_counts": {str(s): int((status == s).sum()) for s in np.unique(status)},
+                   "near_degenerate": int(((bstat & 0x100) != 0).sum()),
                    "wall_s_timed_loop": t_wall},
         "roofline": {"bound": "alu", "kernel": "qp_fwd_kernel", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"{sms} SMs (device properties) x 128 FP32 lanes x 2 x "
+                                    f"{SM_MAX_MHZ:.0f} MHz (nominal; MEASURED_PEAKS.json has no "
+                                    "FP32 figure)",
                      "traffic": profiled_traffic(),
                      "traffic_unit": "bytes per launch (dram read+write, ncu)",
                      "algorithmic_flops_per_launch": f_fwd * B},

@@ -43,12 +43,35 @@ extern "C" {
 #define QP_F32 0  /* FP32 matrices and factors; FP64-accurate residuals and iterate */
 #define QP_F64 1  /* everything in FP64                                              */
 
-/* Per-instance status codes written to status[b]. */
+/* Per-instance status codes written to status[b] by the forward pass, and status words
+ * written by the backward pass when it is given a status array: the low 8 bits hold the code,
+ * higher bits are flags (QP_STATUS_CODE(s) extracts the code; forward statuses carry no
+ * flags). */
 #define QP_STATUS_CONVERGED 0  /* residual and duality tests met                          */
 #define QP_STATUS_MAX_ITER  1  /* max_iter Newton steps taken; iterate returned anyway   */
 #define QP_STATUS_NOT_PD    2  /* a pivot of Q, of A Q⁻¹Aᵀ or of the per-iteration Schur
                                   complement was not positive: outputs are NaN          */
 #define QP_STATUS_NUMERICAL 3  /* a non-finite value appeared: outputs are NaN           */
+#define QP_STATUS_NO_FORWARD 4 /* backward only: the workspace holds no forward pass of this
+                                  instance (no stamp, other sizes, dtype, kernel path or
+                                  Q/G/A buffers): gradients are NaN                     */
+#define QP_STATUS_INFEASIBLE 5 /* infeasibility suspected: the returned λ ≥ 0, ν satisfy
+                                  −(hᵀλ + bᵀν) > 1e3·(1 + ‖z‖∞)·‖Gᵀλ + Aᵀν‖₁, so by Farkas'
+                                  lemma any feasible point has ‖z'‖∞ > 1e3·(1 + ‖z‖∞).
+                                  z, λ, ν are returned, λ and ν scaled so that
+                                  max(‖λ‖∞, ‖ν‖∞) = 1: they are the certificate.  Checked
+                                  once ‖λ‖∞ passes 1e3 × its first-iteration value, and
+                                  when the loop ends on max_iter, the time limit or a
+                                  Newton system that is no longer positive definite.
+                                  Gradients are NaN                                      */
+#define QP_STATUS_TIMEOUT   6  /* the time limit of qp_options ran out; iterate returned
+                                  as for MAX_ITER                                        */
+#define QP_STATUS_CODE(s) ((s) & 0xff)
+/* Flag bit of backward status words: at the returned iterate some complementarity pair has
+ * max(λ_i, s_i) ≤ 1e-5·max(1, max_j max(λ_j, s_j)), a nearly degenerate point where the
+ * proof of Theorem 1 no longer gives a unique derivative (the gradient returned there is
+ * one element of a set). */
+#define QP_FLAG_NEAR_DEGENERATE 0x100
 
 typedef struct qp_options {
   double  tol;       /* stop when ‖r_z‖∞ ≤ tol·(1+‖q‖∞), ‖Gz+s−h‖∞ ≤ tol·(1+‖h‖∞),
@@ -61,11 +84,13 @@ typedef struct qp_options {
                         ‖∂ℓ/∂z*‖∞): one step for well-conditioned systems            */
   int32_t path;      /* 0: automatic kernel choice; 1: always the global-memory kernel.
                         Forward and backward of one batch must use the same value.      */
-  int32_t reserved;  /* set to 0                                                        */
+  int32_t time_limit_us; /* forward only: an instance still iterating this many
+                        microseconds after its block started stops with status
+                        QP_STATUS_TIMEOUT (0 = no limit)                                */
 } qp_options;
 
 /* Default options for a dtype (QP_F32: tol 1e-10, mu_tol 1e-11, max_iter 50, refine 4;
- * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 4; path 0). */
+ * QP_F64: tol 1e-12, mu_tol 1e-13, max_iter 100, refine 4; path 0, no time limit). */
 void qp_default_options(int dtype, qp_options* opt);
 
 /* Bytes of workspace qp_forward needs for B instances of one size (0 on invalid sizes),
@@ -94,7 +119,9 @@ int qp_uses_global_path(int dtype, int n, int nineq, int neq);
  *       μ = sᵀλ/nineq at the returned iterate (status/iters/resid may be NULL).
  * Work: workspace of at least qp_workspace_bytes(dtype,B,n,nineq,neq) bytes, 256-byte
  *       aligned; it keeps the factorisation at the returned iterate and the FP64 iterate
- *       for qp_backward.  It must not be modified between the two calls.
+ *       for qp_backward.  It must not be modified between the two calls.  Each instance's
+ *       slot ends with a stamp (a magic word, the sizes, dtype, kernel path and a hash of
+ *       the instance's Q/G/A addresses) that qp_backward checks on the device.
  * opt:  NULL = qp_default_options(dtype).
  */
 int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
@@ -110,10 +137,14 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
  *   dQ = ½(d_z z*ᵀ + z* d_zᵀ), dq = d_z, dG = d̃_λ z*ᵀ + λ* d_zᵀ, dh = −d̃_λ,
  *   dA = d_ν z*ᵀ + ν* d_zᵀ,    db = −d_ν.
  * Up to `refine` steps of iterative refinement with an FP64-accurate KKT residual follow
- * the first solve (see qp_options).  Q, G, A must be the same data passed to qp_forward (they feed the
- * refinement residual).  dl_dz [B,n] is ∂ℓ/∂z*.  Any gradient pointer may be NULL
- * (not wanted).  Instances whose forward status was NOT_PD or NUMERICAL get NaN
- * gradients.
+ * the first solve (see qp_options).  Q, G, A must be the same buffers, holding the same
+ * data, as passed to qp_forward (they feed the refinement residual).  dl_dz [B,n] is
+ * ∂ℓ/∂z*.  Any gradient pointer may be NULL (not wanted).  Instances whose forward status
+ * was NOT_PD, NUMERICAL or INFEASIBLE get NaN gradients; so do instances whose workspace
+ * stamp does not match this call (no forward of these sizes, dtype, kernel path and Q/G/A
+ * buffers ran on it: QP_STATUS_NO_FORWARD).  A stamp cannot tell whether the data in the
+ * buffers changed since the forward pass.  Call-level errors as qp_forward (the host
+ * checks the workspace size); nothing is synchronised.
  */
 int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
                 const void* Q, const void* G, const void* A,
@@ -121,7 +152,8 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                 void* dQ, void* dq, void* dG, void* dh, void* dA, void* db, void* stream);
 
 /*
- * qp_backward_ext -- qp_backward for a loss that also depends on λ* and ν*.
+ * qp_backward_ext -- qp_backward for a loss that also depends on λ* and ν*, with an
+ * optional per-instance status output.
  *
  * §3 differentiates z* only (it sets the λ*, ν* case aside).  The same implicit
  * differentiation of Eq. 6 gives, for a loss of (z*, λ*, ν*), the adjoint of Eq. 7 with
@@ -130,14 +162,18 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
  * feasibility rows: K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z*; 0; −∂ℓ/∂λ*; −∂ℓ/∂ν*].
  *
  * dl_dlam: [B, nineq] and dl_dnu: [B, neq], device memory of the dtype, row-major; either
- * may be null (zero).  dl_dz is required (pass zeros for a loss of λ*, ν* alone).  All other
- * arguments, outputs and errors as qp_backward; qp_backward(...) is this call with both null.
+ * may be null (zero).  dl_dz is required (pass zeros for a loss of λ*, ν* alone).
+ * status: [B] int32 device memory or NULL; receives the forward pass's status code of each
+ * instance, or QP_STATUS_NO_FORWARD when its workspace stamp does not match.  All other
+ * arguments, outputs and errors as qp_backward; qp_backward(...) is this call with
+ * dl_dlam, dl_dnu and status null.
  */
 int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
                     const void* Q, const void* G, const void* A,
                     const void* workspace, size_t workspace_bytes, const void* dl_dz,
                     const void* dl_dlam, const void* dl_dnu,
-                    void* dQ, void* dq, void* dG, void* dh, void* dA, void* db, void* stream);
+                    void* dQ, void* dq, void* dG, void* dh, void* dA, void* db,
+                    int32_t* status, void* stream);
 
 /*
  * Packed batches of uneven sizes (one persistent launch each way).
@@ -194,12 +230,14 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
 /* Backward pass of a packed batch, after qp_forward_packed with the same desc, sizes and
  * workspace.  dl_dz is packed like z; the gradients like the inputs.  It differentiates a
  * loss of z* (for a loss that also depends on λ*, ν*, use qp_backward_ext on a fixed-size
- * batch). */
+ * batch).  status (int32 [B] indexed by instance id, or NULL) as in qp_backward_ext.  The
+ * workspace is written: bytes 4..7 hold the backward pass's work-queue counter, so two
+ * backward calls on one workspace must not overlap on the GPU. */
 int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
                        const qp_packed_sizes* sizes, const void* Q, const void* G,
-                       const void* A, const void* workspace, size_t workspace_bytes,
+                       const void* A, void* workspace, size_t workspace_bytes,
                        const void* dl_dz, void* dQ, void* dq, void* dG, void* dh, void* dA,
-                       void* db, void* stream);
+                       void* db, int32_t* status, void* stream);
 
 /*
  * qp_forward_noalloc -- qp_forward for callers that cannot allocate device memory (a control
@@ -212,7 +250,9 @@ int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instanc
  * library until exit) takes its place.  It allocates nothing.  Returns QP_ENOSPACE when
  * qp_workspace_bytes_opt() for the call exceeds QP_NOALLOC_SCRATCH_BYTES (e.g. about 170
  * instances of n = 100, nineq = 100, neq = 50 in FP32).  The first call on a device looks up
- * the array's address there (make it before any stream capture).  All calls share the
+ * the array's address there (make it before any stream capture) and caches it for the life of
+ * the process; after a cudaDeviceReset of that device the cached address is stale, so do not
+ * call this entry point on a device that was reset.  All calls share the
  * array, so calls that overlap on the GPU race; its contents after a call are that call's
  * factorisation, which is not reachable from qp_backward.
  */

@@ -77,7 +77,7 @@ c_int, c_size_t, c_void_p, c_double = ctypes.c_int, ctypes.c_size_t, ctypes.c_vo
 class QPOptions(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("mu_tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("path", ctypes.c_int32), ("time_limit_us", ctypes.c_int32)]
 
 
 class QPInstanceDesc(ctypes.Structure):
@@ -103,7 +103,7 @@ EXPORTS = {
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                     + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 8),
     "qp_backward_ext": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
-                        + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 10),
+                        + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 11),
     "qp_strerror": (ctypes.c_char_p, [c_int]),
     "qp_host_copy_many": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int]),
     "qp_forward_noalloc": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
@@ -117,7 +117,7 @@ EXPORTS = {
                                   ctypes.POINTER(QPPackedSizes)] + [c_void_p] * 13 + [c_size_t, c_void_p]),
     "qp_backward_packed": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,
                                    ctypes.POINTER(QPPackedSizes)] + [c_void_p] * 4 + [c_size_t]
-                           + [c_void_p] * 8),
+                           + [c_void_p] * 9),
 }
 
 

@@ -9,14 +9,18 @@ from __future__ import annotations
 
 import torch
 
-from .qp import qp_backward, qp_forward
+from .qp import ForwardResult, qp_backward, qp_forward
 
 
 class QPFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, Q, q, G, h, A, b, options=None):
         fwd = qp_forward(Q, q, G, h, A, b, options=options)
-        ctx.fwd = fwd
+        # Tensors go through save_for_backward (autograd's version checks catch an in-place
+        # change of Q, G or A before the backward pass, and no reference cycle keeps the
+        # workspace alive); only option and shape metadata stay on ctx.
+        ctx.save_for_backward(fwd.Q, fwd.G, fwd.A, fwd.z, fwd.lam, fwd.nu, fwd.workspace)
+        ctx.options = fwd.options
         ctx.shapes = (G is None, A is None)
         ctx.mark_non_differentiable(fwd.status)
         ctx.set_materialize_grads(False)   # unused outputs' gradients arrive as None
@@ -26,10 +30,12 @@ class QPFunction(torch.autograd.Function):
     def backward(ctx, dz, dlam, dnu, dstatus):
         if dz is None and dlam is None and dnu is None:
             return (None,) * 7
+        Qc, Gc, Ac, z, lam, nu, ws = ctx.saved_tensors
+        fwd = ForwardResult(z, lam, nu, None, None, None, ws, Qc, Gc, Ac, ctx.options)
         if dz is None:
-            dz = torch.zeros_like(ctx.fwd.z)
+            dz = torch.zeros_like(z)
         need = ctx.needs_input_grad[:6]
-        g = qp_backward(ctx.fwd, dz, dl_dlam=dlam, dl_dnu=dnu,
+        g = qp_backward(fwd, dz, dl_dlam=dlam, dl_dnu=dnu,
                         need=tuple(bool(x) for x in need))
         no_g, no_a = ctx.shapes
         grads = list(g)

@@ -156,7 +156,7 @@ void qp_default_options(int dtype, qp_options* opt) {
   }
   opt->refine = 4;
   opt->path = 0;
-  opt->reserved = 0;
+  opt->time_limit_us = 0;
 }
 
 size_t qp_workspace_bytes(int dtype, int B, int n, int nineq, int neq) {
@@ -192,7 +192,8 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
   if (((uintptr_t)workspace) % 256 != 0) return QP_EINVAL;
   qp_options o;
   if (opt) o = *opt; else qp_default_options(dtype, &o);
-  if (o.max_iter < 0 || o.path < 0 || o.path > 1) return QP_EINVAL;
+  if (o.max_iter < 0 || o.path < 0 || o.path > 1 || o.time_limit_us < 0) return QP_EINVAL;
+  const unsigned long long tl_ns = 1000ull * (unsigned long long)o.time_limit_us;
   const Plan pl = make_plan(dtype, n, nineq, neq, o.path);
   if (workspace_bytes < (size_t)B * pl.ws) return QP_ENOSPACE;
   if (!pl.ok) return QP_EUNSUPPORTED;
@@ -203,7 +204,7 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
                             (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
                             (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
                             status, iters, resid, (unsigned char*)workspace,
-                            pl.ws, o.tol, o.mu_tol, o.max_iter};
+                            pl.ws, o.tol, o.mu_tol, o.max_iter, tl_ns};
     e = pl.large ? qpk::launch_fwd_large_f32(P, pl.fsmem, st)
                  : qpk::launch_fwd_f32(P, pl.sw, pl.ch, pl.fsmem, st);
   } else {
@@ -211,7 +212,7 @@ int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int ne
                              (const double*)Q, (const double*)q, (const double*)G, (const double*)h,
                              (const double*)A, (const double*)b, (double*)z, (double*)lam,
                              (double*)nu, status, iters, resid, (unsigned char*)workspace,
-                             pl.ws, o.tol, o.mu_tol, o.max_iter};
+                             pl.ws, o.tol, o.mu_tol, o.max_iter, tl_ns};
     e = pl.large ? qpk::launch_fwd_large_f64(P, pl.fsmem, st)
                  : qpk::launch_fwd_f64(P, pl.sw, pl.ch, pl.fsmem, st);
   }
@@ -223,14 +224,14 @@ int qp_backward(const qp_options* opt, int dtype, int B, int n, int nineq, int n
                 size_t workspace_bytes, const void* dl_dz, void* dQ, void* dq, void* dG,
                 void* dh, void* dA, void* db, void* stream) {
   return qp_backward_ext(opt, dtype, B, n, nineq, neq, Q, G, A, workspace, workspace_bytes,
-                         dl_dz, nullptr, nullptr, dQ, dq, dG, dh, dA, db, stream);
+                         dl_dz, nullptr, nullptr, dQ, dq, dG, dh, dA, db, nullptr, stream);
 }
 
 int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
                     const void* Q, const void* G, const void* A, const void* workspace,
                     size_t workspace_bytes, const void* dl_dz, const void* dl_dlam,
                     const void* dl_dnu, void* dQ, void* dq, void* dG, void* dh, void* dA,
-                    void* db, void* stream) {
+                    void* db, int32_t* status, void* stream) {
   if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(B, n, nineq, neq)) return QP_EINVAL;
   if (B == 0) return QP_OK;
   if (!Q || !dl_dz || !workspace) return QP_EINVAL;
@@ -251,7 +252,8 @@ int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, i
                             (const float*)Q, (const float*)G, (const float*)A,
                             (const float*)dl_dz, (float*)dQ, (float*)dq, (float*)dG, (float*)dh,
                             (float*)dA, (float*)db, (const unsigned char*)workspace,
-                            pl.ws, o.refine, (const float*)dl_dlam, (const float*)dl_dnu};
+                            pl.ws, o.refine, (const float*)dl_dlam, (const float*)dl_dnu,
+                            status};
     e = qpk::launch_bwd_f32(P, smem, st);
   } else {
     qpk::BwdParams<double> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0,
@@ -259,7 +261,7 @@ int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, i
                              (const double*)A, (const double*)dl_dz, (double*)dQ, (double*)dq,
                              (double*)dG, (double*)dh, (double*)dA, (double*)db,
                              (const unsigned char*)workspace, pl.ws, o.refine,
-                             (const double*)dl_dlam, (const double*)dl_dnu};
+                             (const double*)dl_dlam, (const double*)dl_dnu, status};
     e = qpk::launch_bwd_f64(P, smem, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;
@@ -345,7 +347,8 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
   if ((size_t)sizes->fwd_smem > (size_t)max_smem_optin()) return QP_EUNSUPPORTED;
   qp_options o;
   if (opt) o = *opt; else qp_default_options(dtype, &o);
-  if (o.max_iter < 0) return QP_EINVAL;
+  if (o.max_iter < 0 || o.time_limit_us < 0) return QP_EINVAL;
+  const unsigned long long tl_ns = 1000ull * (unsigned long long)o.time_limit_us;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(workspace, 0, 8, st) != cudaSuccess) return QP_ECUDA;
   const int grid = std::min(B, num_sms());
@@ -355,7 +358,7 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
                                   (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
                                   (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
                                   status, iters, resid, (unsigned char*)workspace,
-                                  o.tol, o.mu_tol, o.max_iter};
+                                  o.tol, o.mu_tol, o.max_iter, tl_ns};
     e = qpk::launch_fwd_packed_f32(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
                                       sizes->n_global > 0, st);
   } else {
@@ -363,7 +366,7 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
                                    (const double*)Q, (const double*)q, (const double*)G,
                                    (const double*)h, (const double*)A, (const double*)b,
                                    (double*)z, (double*)lam, (double*)nu, status, iters, resid,
-                                   (unsigned char*)workspace, o.tol, o.mu_tol, o.max_iter};
+                                   (unsigned char*)workspace, o.tol, o.mu_tol, o.max_iter, tl_ns};
     e = qpk::launch_fwd_packed_f64(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
                                       sizes->n_global > 0, st);
   }
@@ -372,9 +375,9 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
 
 int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
                        const qp_packed_sizes* sizes, const void* Q, const void* G,
-                       const void* A, const void* workspace, size_t workspace_bytes,
+                       const void* A, void* workspace, size_t workspace_bytes,
                        const void* dl_dz, void* dQ, void* dq, void* dG, void* dh, void* dA,
-                       void* db, void* stream) {
+                       void* db, int32_t* status, void* stream) {
   if ((dtype != QP_F32 && dtype != QP_F64) || B < 0 || !sizes) return QP_EINVAL;
   if (B == 0) return QP_OK;
   if (!desc || !Q || !dl_dz || !workspace) return QP_EINVAL;
@@ -389,20 +392,21 @@ int qp_backward_packed(const qp_options* opt, int dtype, int B, const qp_instanc
   // The backward counter is the second int of the workspace (the forward leaves it alone).
   if (cudaMemsetAsync((char*)workspace + 4, 0, 4, st) != cudaSuccess) return QP_ECUDA;
   const int grid = std::min(B, num_sms());
-  int* ctr = (int*)((char*)const_cast<void*>(workspace) + 4);
+  int* ctr = (int*)((char*)workspace + 4);
   cudaError_t e;
   if (dtype == QP_F32) {
     qpk::PackedBwdParams<float> P{B, (const qpk::PackedDesc*)desc, ctr, (const float*)Q,
                                   (const float*)G, (const float*)A, (const float*)dl_dz,
                                   (float*)dQ, (float*)dq, (float*)dG, (float*)dh, (float*)dA,
-                                  (float*)db, (const unsigned char*)workspace, o.refine};
+                                  (float*)db, (const unsigned char*)workspace, o.refine,
+                                  status};
     e = qpk::launch_bwd_packed_f32(P, (size_t)sizes->bwd_smem, grid, st);
   } else {
     qpk::PackedBwdParams<double> P{B, (const qpk::PackedDesc*)desc, ctr, (const double*)Q,
                                    (const double*)G, (const double*)A, (const double*)dl_dz,
                                    (double*)dQ, (double*)dq, (double*)dG, (double*)dh,
                                    (double*)dA, (double*)db, (const unsigned char*)workspace,
-                                   o.refine};
+                                   o.refine, status};
     e = qpk::launch_bwd_packed_f64(P, (size_t)sizes->bwd_smem, grid, st);
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;

@@ -19,8 +19,9 @@
 // X = L⁻¹ in the same column loop, so every triangular solve is a product with X or Xᵀ.
 //
 // Precision.  T is the matrix/factor type (float or double).  The iterate (z, s, λ, ν)
-// is kept in FP64, and the KKT residual, the convergence test, the step lengths and the
-// backward refinement residual are FP64-accurate.  For T = float the residual products
+// is kept in FP64, and the KKT residual vectors and the backward refinement residual are
+// FP64-accurate; the norms of the stopping test, μ and the step-length reductions are FP32
+// reductions in both dtypes (enough for them).  For T = float the residual products
 // use error-free FP32 transformations (Dekker's product by FMA and Knuth's two-sum), a
 // double-float accumulation whose error is about 2⁻⁴⁸ of Σ|terms|, because the FP64 pipe
 // of this part is a small fraction of the FP32 rate.  The Newton directions themselves
@@ -53,7 +54,23 @@ __host__ __device__ inline bool reg_chol_ok(int p, int esz) {
   return nt <= NTHREADS || (esz == 4 && nt <= 2 * NTHREADS && p <= REG_CHOL_MAX_P);
 }
 
-enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3 };
+enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3, ST_NOFWD = 4, ST_INFEAS = 5,
+             ST_TIMEOUT = 6 };
+// Flag bit of the status word kept in the workspace (reported by the backward pass): a nearly
+// degenerate complementarity pair at the returned iterate.
+constexpr int FLAG_NEARDEG = 0x100;
+// Magic word of the workspace stamp the forward pass leaves for the backward pass.
+constexpr int32_t STAMP_MAGIC = 0x51504657;
+
+// 32-bit mix of an instance's Q, G and A addresses (part of the workspace stamp), so that a
+// backward pass given other buffers than its forward pass is detected.
+__host__ __device__ inline int32_t stamp_hash(const void* Q, const void* G, const void* A) {
+  unsigned long long h = (unsigned long long)(uintptr_t)Q * 0x9E3779B97F4A7C15ull;
+  h ^= (unsigned long long)(uintptr_t)G * 0xC2B2AE3D27D4EB4Full;
+  h ^= (unsigned long long)(uintptr_t)A * 0x165667B19E3779F9ull;
+  h ^= h >> 29;
+  return (int32_t)(uint32_t)(h ^ (h >> 32));
+}
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -66,7 +83,9 @@ __host__ __device__ inline int padded_nz(int n, int m) { return n + ((4 - (n + m
 // Per-instance workspace (global memory) kept from forward to backward.
 // Layout shared by both kernel paths (the backward pass reads only this prefix):
 // SR = [S; RE] ((m1+p) × m1, m1 = nz + neq), the p×p block with X = L⁻¹ (lower) and M
-// (strict upper), the FP64 iterate (z, s, λ, ν) and the status word.  The global-memory
+// (strict upper), the FP64 iterate (z, s, λ, ν) and the stamp: eight int32 words
+// {status code | flags, STAMP_MAGIC, n, nineq, neq, element size | path << 8, nz,
+// stamp_hash(Q, G, A)} that the backward pass checks before it trusts the rest.  The global-memory
 // path appends diag(M), its Cholesky work matrix (row stride round4(p)) and its panel
 // scratch (the sweep's two 16-row panels, or the Cholesky's panel and staging buffer).
 struct WsLayout {
@@ -77,7 +96,7 @@ struct WsLayout {
     oX = align_up(oSR + (m1 + p) * m1 * esz, 256);
     oIt = align_up(oX + (size_t)p * p * esz, 256);
     oSt = align_up(oIt + 8 * ((size_t)n + 2 * (size_t)p + m), 256);
-    size_t o = align_up(oSt + 16, 256);
+    size_t o = align_up(oSt + 32, 256);
     odM = oAw = oPan = o;
     if (large) {
       const size_t N = m1 + p, ldp = (N + 7) / 8 * 8;
@@ -192,6 +211,7 @@ struct FwdParams {
   size_t ws_inst;
   double tol, mu_tol;
   int max_iter;
+  unsigned long long time_limit_ns;   // 0: none
 };
 
 // Per-instance views used by the kernel bodies (built from the fixed-size parameters or from
@@ -206,6 +226,7 @@ struct FwdInst {
   unsigned char* ws;         // this instance's workspace
   double tol, mu_tol;
   int max_iter;
+  unsigned long long time_limit_ns;   // 0: none
 };
 
 template <typename T>
@@ -216,6 +237,7 @@ struct BwdInst {
   const unsigned char* ws;
   int refine;
   const T *dl_dlam, *dl_dnu;   // ∂ℓ/∂λ*, ∂ℓ/∂ν* of this instance (or null: zero)
+  int32_t* status;             // this instance's backward status slot (or null)
 };
 
 // Descriptor of one instance of a packed (uneven) batch; the C ABI's qp_instance_desc has
@@ -237,6 +259,7 @@ struct PackedFwdParams {
   unsigned char* ws;
   double tol, mu_tol;
   int max_iter;
+  unsigned long long time_limit_ns;
 };
 
 template <typename T>
@@ -248,6 +271,7 @@ struct PackedBwdParams {
   T *dQ, *dq, *dG, *dh, *dA, *db;
   const unsigned char* ws;
   int refine;
+  int32_t* status;   // [B] by instance id, or null
 };
 
 template <typename T>
@@ -260,6 +284,7 @@ struct BwdParams {
   size_t ws_inst;
   int refine;
   const T *dl_dlam, *dl_dnu;   // [B, nineq], [B, neq] or null (zero)
+  int32_t* status;             // [B] or null
 };
 
 // ------------------------------------------------------------------ FP64-accurate dot products
@@ -1073,6 +1098,13 @@ __device__ __forceinline__ void mv_sym_upper(int p, const T* Mb, int ldM, const 
   mv_cols(Mb, ldM, p, p, TRI_SUPPER, x, scr, [&](int c, T v) { out[c] = tmp[c] + v; });
 }
 
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // s/λ rounded into the factor type, kept finite and non-zero.
 template <typename T> __device__ __forceinline__ T ratio_to(T r);
 template <> __device__ __forceinline__ float ratio_to<float>(float r) {
@@ -1114,10 +1146,13 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
   T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p, *mdl = dsh + p, *tmp = mdl + p;
   T *dsv = tmp + p, *ccv = dsv + p;
   float* red = reinterpret_cast<float*>(sm + L.ored);
+  double* dred = reinterpret_cast<double*>(sm + L.ored);
   Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.ocb);
   T* tscr = reinterpret_cast<T*>(sm + L.ocb);
   const int kscr = (int)(L.cbytes / sizeof(Acc<T>));
   (void)cb;
+  __shared__ int s_timeout;
+  const unsigned long long t_start = P.time_limit_ns ? globaltimer_ns() : 0ull;
 
   const T* Qb = P.Q;
   const T* qb = P.q;
@@ -1134,8 +1169,41 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
   int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
   const int ldS = m1, ldM = p > 0 ? p : 1;
 
-  int status = ST_CONV, it = 0, extra = 0;
+  int status = ST_CONV, it = 0, extra = 0, flags = 0;
   float last[4] = {0.f, 0.f, 0.f, 0.f};   // residual norms and μ at the returned iterate
+  double cert_scale = 1.0;                 // 1/max(‖λ‖∞, ‖ν‖∞) of an infeasibility certificate
+
+  // Certificate of infeasibility (Farkas' lemma) from the current λ ≥ 0, ν: for any z' with
+  // Gz' ≤ h, Az' = b, (Gᵀλ + Aᵀν)ᵀz' ≤ hᵀλ + bᵀν, so −(hᵀλ + bᵀν) > R·‖Gᵀλ + Aᵀν‖₁ rules out
+  // feasible points with ‖z'‖∞ ≤ R.  Taken with R = 1e3·(1 + ‖z‖∞): at a feasible KKT point
+  // the ratio is at most ‖z‖∞ (Gᵀλ + Aᵀν = −(Qz + q) there), while along a diverging Farkas
+  // direction it grows with ‖λ‖ until the FP32 Newton system turns singular (near 1e4 in
+  // small examples).  Uses rz/rl/rn and xs as scratch; true on every thread when it holds.
+  auto infeasible_cert = [&]() -> bool {
+    for (int i = tid; i < n + p + m; i += NTHREADS)
+      xs[i] = Split<T>::make(i < n ? 0.0 : (i < n + p ? lam[i - n] : nu[i - n - p]));
+    __syncthreads();
+    kkt_apply<T>(n, p, m, P.Q, p ? P.G : nullptr, m ? P.A : nullptr, xs, ascr, kscr,
+                 [&](int) { return 0.0; }, [&](int) { return 0.0; }, [&](int) { return 0.0; },
+                 rz, rl, rn);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < p; i += NTHREADS) {
+      v[0] -= hd[i] * lam[i];
+      v[3] = fmax(v[3], fabs(lam[i]));
+    }
+    for (int i = tid; i < m; i += NTHREADS) {
+      v[0] -= bd[i] * nu[i];
+      v[3] = fmax(v[3], fabs(nu[i]));
+    }
+    for (int i = tid; i < n; i += NTHREADS) {
+      v[1] += fabs(rz[i]);
+      v[2] = fmax(v[2], fabs(z[i]));
+    }
+    block_reduce4<R_SUM, R_SUM, R_MAX, R_MAX>(v, dred);
+    cert_scale = v[3] > 0.0 ? 1.0 / v[3] : 1.0;
+    return v[0] > 0.0 && v[0] > 1e3 * (1.0 + v[2]) * v[1];
+  };
+
   bool ok = setup(Qb, Ab, Gb);
   __syncthreads();
   if (!ok) status = ST_NOTPD;
@@ -1224,7 +1292,17 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
       __syncthreads();
 
       // ---- interior point iterations
+      float lam_max = 0.f, lam_check = INFINITY;   // ‖λ‖∞ and the level that triggers a
+                                                    // certificate check (1e3 × its first value)
+      bool loop_notpd = false;                      // a Newton step's factorisation failed
       for (it = 0;; ++it) {
+        if (lam_max > lam_check) {
+          if (infeasible_cert()) {
+            status = ST_INFEAS;
+            break;
+          }
+          lam_check *= 1e3f;
+        }
         for (int i = tid; i < n + p + m; i += NTHREADS)
           xs[i] = Split<T>::make(i < n ? z[i] : (i < n + p ? lam[i - n] : nu[i - n - p]));
         __syncthreads();
@@ -1278,11 +1356,22 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
           status = ST_MAXIT;
           break;
         }
+        if (P.time_limit_ns) {
+          if (tid == 0) s_timeout = (globaltimer_ns() - t_start > P.time_limit_ns) ? 1 : 0;
+          __syncthreads();
+          const int out = s_timeout;
+          __syncthreads();
+          if (out) {
+            status = ST_TIMEOUT;
+            break;
+          }
+        }
         for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>((T)s[i] / (T)lam[i]);
         for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
         __syncthreads();
         if (!factor(dsh)) {
           status = ST_NOTPD;
+          loop_notpd = true;
           break;
         }
         // Affine-scaling (predictor) direction, Eq. 9.
@@ -1302,9 +1391,12 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
           dsv[i] = dsai;
           if (dsai < T(0)) w4[0] = fminf(w4[0], (float)(-si / dsai));
           if (d < T(0)) w4[0] = fminf(w4[0], (float)(-li / d));
+          w4[1] = fmaxf(w4[1], (float)li);
         }
-        block_reduce4f<R_MIN, R_SUM, R_SUM, R_SUM>(w4, red);
+        block_reduce4f<R_MIN, R_MAX, R_SUM, R_SUM>(w4, red);
         const float a_aff = fminf(1.f, w4[0]);
+        lam_max = w4[1];
+        if (it == 0) lam_check = 1e3f * fmaxf(1.f, lam_max);
         float w5[4] = {0.f, 0.f, 0.f, 0.f};
         for (int i = tid; i < p; i += NTHREADS) {
           const T si = (T)s[i], li = (T)lam[i];
@@ -1344,11 +1436,26 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
         }
         __syncthreads();
       }
+      // An interior point loop that ran out of steps or time, or whose Newton system became
+      // singular, may be facing infeasible data (λ diverging along a Farkas direction).
+      if ((status == ST_MAXIT || status == ST_TIMEOUT || loop_notpd) && infeasible_cert())
+        status = ST_INFEAS;
       // Factorisation at the returned iterate: the one the backward pass reuses.
-      if (status == ST_CONV || status == ST_MAXIT) {
+      if (status == ST_CONV || status == ST_MAXIT || status == ST_TIMEOUT) {
         for (int i = tid; i < p; i += NTHREADS) dsh[i] = ratio_to<T>((T)s[i] / (T)lam[i]);
         __syncthreads();
         if (!factor(dsh)) status = ST_NOTPD;
+      }
+      // Near-degenerate point: some pair with max(λ_i, s_i) ≤ 1e-5·max(1, max_j max(λ_j, s_j)).
+      if (status == ST_CONV || status == ST_MAXIT || status == ST_TIMEOUT) {
+        float w[4] = {INFINITY, 0.f, 0.f, 0.f};
+        for (int i = tid; i < p; i += NTHREADS) {
+          const float mx = fmaxf((float)s[i], (float)lam[i]);
+          w[0] = fminf(w[0], mx);
+          w[1] = fmaxf(w[1], mx);
+        }
+        block_reduce4f<R_MIN, R_MAX, R_SUM, R_SUM>(w, red);
+        if (w[0] <= 1e-5f * fmaxf(1.f, w[1])) flags |= FLAG_NEARDEG;
       }
     }
   }
@@ -1356,26 +1463,35 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
   // ---- outputs and the state kept for the backward pass
   const bool bad = (status == ST_NOTPD || status == ST_NUM);
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  // An infeasibility certificate is returned scaled to max(‖λ‖∞, ‖ν‖∞) = 1.
+  const double dsc = status == ST_INFEAS ? cert_scale : 1.0;
   for (int i = tid; i < n; i += NTHREADS) {
     const double v = bad ? qnan : z[i];
     P.z[i] = (T)v;
     wIt[i] = v;
   }
   for (int i = tid; i < p; i += NTHREADS) {
-    const double vs = bad ? qnan : s[i], vl = bad ? qnan : lam[i];
+    const double vs = bad ? qnan : s[i], vl = bad ? qnan : lam[i] * dsc;
     if (P.lam) P.lam[i] = (T)vl;
     wIt[n + i] = vs;
     wIt[n + p + i] = vl;
   }
   for (int i = tid; i < m; i += NTHREADS) {
-    const double v = bad ? qnan : nu[i];
+    const double v = bad ? qnan : nu[i] * dsc;
     if (P.nu) P.nu[i] = (T)v;
     wIt[n + 2 * p + i] = v;
   }
   if (!bad && !ws_resident)
     for (int i = tid; i < p * p; i += NTHREADS) wX[i] = Mb[i];
   if (tid == 0) {
-    wSt[0] = status;
+    wSt[0] = status | flags;
+    wSt[1] = STAMP_MAGIC;
+    wSt[2] = n;
+    wSt[3] = p;
+    wSt[4] = m;
+    wSt[5] = (int32_t)sizeof(T) | (ws_resident ? 256 : 0);
+    wSt[6] = nz;
+    wSt[7] = stamp_hash(P.Q, p ? P.G : nullptr, m ? P.A : nullptr);
     if (P.status) *P.status = status;
     if (P.iters) *P.iters = it;
     if (P.resid) {
@@ -1407,6 +1523,7 @@ __device__ __forceinline__ FwdInst<T> fixed_inst(const FwdParams<T>& P, int bi) 
   I.resid = P.resid ? P.resid + 4 * (size_t)bi : nullptr;
   I.ws = P.ws + (size_t)bi * P.ws_inst;
   I.tol = P.tol; I.mu_tol = P.mu_tol; I.max_iter = P.max_iter;
+  I.time_limit_ns = P.time_limit_ns;
   return I;
 }
 
@@ -1508,6 +1625,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const Packed
     I.resid = P.resid ? P.resid + 4 * (size_t)d.id : nullptr;
     I.ws = P.ws + d.ows;
     I.tol = P.tol; I.mu_tol = P.mu_tol; I.max_iter = P.max_iter;
+    I.time_limit_ns = P.time_limit_ns;
     if (d.flags & 1) {
       if constexpr (WITH_GLOBAL) {
         fwd_global_path<T>(I, sm);
@@ -1551,15 +1669,23 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   const T* SR = reinterpret_cast<const T*>(wsb + W.oSR);
   const T* X = reinterpret_cast<const T*>(wsb + W.oX);
   const double* wIt = reinterpret_cast<const double*>(wsb + W.oIt);
-  const int status = reinterpret_cast<const int32_t*>(wsb + W.oSt)[0];
   const T* Qb = P.Q;
   const T* Gb = p ? P.G : nullptr;
   const T* Ab = m ? P.A : nullptr;
+  // The stamp the forward pass left: trusted only if it names this instance's sizes, element
+  // type, kernel path and Q/G/A buffers.
+  const int32_t* stp = reinterpret_cast<const int32_t*>(wsb + W.oSt);
+  const bool stamped = stp[1] == STAMP_MAGIC && stp[2] == n && stp[3] == p && stp[4] == m &&
+                       stp[5] == ((int32_t)sizeof(T) | (P.large ? 256 : 0)) && stp[6] == nz &&
+                       stp[7] == stamp_hash(Qb, Gb, Ab);
+  const int sword = stamped ? stp[0] : ST_NOFWD;
+  const int status = sword & 0xff;
+  if (tid == 0 && P.status) *P.status = sword;
   const T* gz = P.dl_dz;
   const T* gl = P.dl_dlam;   // may be null: zero
   const T* gn = P.dl_dnu;    // may be null: zero
 
-  if (status == ST_NOTPD || status == ST_NUM) {
+  if (status == ST_NOTPD || status == ST_NUM || status == ST_NOFWD || status == ST_INFEAS) {
     const T qn = (T)__longlong_as_double(0x7ff8000000000000LL);
     if (P.dQ) for (int i = tid; i < n * n; i += NTHREADS) P.dQ[i] = qn;
     if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[i] = qn;
@@ -1724,6 +1850,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   I.refine = P.refine;
   I.dl_dlam = P.dl_dlam ? P.dl_dlam + (size_t)bi * p : nullptr;
   I.dl_dnu = P.dl_dnu ? P.dl_dnu + (size_t)bi * m : nullptr;
+  I.status = P.status ? P.status + bi : nullptr;
   bwd_body<T>(I, sm);
 }
 
@@ -1755,6 +1882,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_packed_kernel(const Packed
     I.refine = P.refine;
     I.dl_dlam = nullptr;   // the packed entry takes ∂ℓ/∂z* only
     I.dl_dnu = nullptr;
+    I.status = P.status ? P.status + d.id : nullptr;
     bwd_body<T>(I, sm);
     __syncthreads();
   }

@@ -11,7 +11,10 @@
 // when the library's module is loaded on a device and held by every device that loads it
 // until the process exits.  Its device address is looked up once per device, with that device
 // current, the first time the entry point runs there; do that first call before any stream
-// capture.  Every call shares the array and leaves its contents behind: the forward kernel
+// capture.  The address is then cached for the life of the process: a cudaDeviceReset (or any
+// other teardown of the device's primary context) reloads the module at a new address and
+// leaves the cached one dangling, so callers that reset a device must not call this entry
+// point on it afterwards.  Every call shares the array and leaves its contents behind: the forward kernel
 // writes everything it later reads, so nothing has to be cleared between calls, but calls
 // that overlap on the GPU (different streams, or a second call before the first finished)
 // race on it.

@@ -128,7 +128,9 @@ class PackedBatch:
         _check(rc)
         return out
 
-    def backward(self, Q, G, A, dl_dz, out=None):
+    def backward(self, Q, G, A, dl_dz, out=None, status=None):
+        """Gradients packed like the inputs; ``status`` (int32 [B] CUDA tensor, by instance
+        index) receives each instance's backward status word when given."""
         lib = _lib.load()
         dev = self.device
         if out is None:
@@ -139,7 +141,7 @@ class PackedBatch:
                 ctypes.byref(self.options), self.code, self.B,
                 ctypes.c_void_p(self.desc.data_ptr()), ctypes.byref(self.sizes),
                 _ptr(Q), _ptr(self._buf(G)), _ptr(self._buf(A)), _ptr(self.workspace),
-                self.workspace.numel(), _ptr(dl_dz), *[_ptr(g) for g in out],
+                self.workspace.numel(), _ptr(dl_dz), *[_ptr(g) for g in out], _ptr(status),
                 _stream_handle(dev))
         _check(rc)
         return out

@@ -19,6 +19,8 @@ from . import _lib
 
 QP_F32, QP_F64 = 0, 1
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NOT_PD, STATUS_NUMERICAL = 0, 1, 2, 3
+STATUS_NO_FORWARD, STATUS_INFEASIBLE, STATUS_TIMEOUT = 4, 5, 6
+FLAG_NEAR_DEGENERATE = 0x100   # in backward status words (status & 0xff is the code)
 
 
 class QPError(RuntimeError):
@@ -151,10 +153,13 @@ def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=
 
 
 def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, dl_dlam=None, dl_dnu=None,
-                need=(True,) * 6, options=None, out=None):
+                need=(True,) * 6, options=None, out=None, status=None):
     """Gradients (dQ, dq, dG, dh, dA, db) of ℓ(z*) (C ABI ``qp_backward``), or of ℓ(z*, λ*, ν*)
     when ``dl_dlam`` ([B, nineq]) or ``dl_dnu`` ([B, neq]) is given (``qp_backward_ext``);
-    entries for which ``need`` is False come back as None."""
+    entries for which ``need`` is False come back as None.  ``status``: an int32 [B] CUDA
+    tensor that receives each instance's backward status word (forward status code, or
+    STATUS_NO_FORWARD when the workspace holds no matching forward pass; flag bits above the
+    low 8, e.g. FLAG_NEAR_DEGENERATE)."""
     Q, G, A = fwd.Q, fwd.G, fwd.A
     B, n, nineq, neq = Q.shape[0], Q.shape[1], G.shape[1], A.shape[1]
     dev, dt = Q.device, Q.dtype
@@ -175,8 +180,11 @@ def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, dl_dlam=None, dl_dnu
             if tuple(t.shape) != (B, k):
                 raise QPError(f"{name} has shape {tuple(t.shape)}, expected {(B, k)}")
         extra.append(t if t is not None and t.numel() else None)
+    if status is not None and (status.dtype != torch.int32 or status.device != dev
+                               or status.numel() < B or not status.is_contiguous()):
+        raise QPError("status must be a contiguous int32 tensor of B elements on the device")
     with torch.cuda.device(dev):
-        if extra[0] is None and extra[1] is None:
+        if extra[0] is None and extra[1] is None and status is None:
             rc = lib.qp_backward(ctypes.byref(opts), _dtype_code(Q), B, n, nineq, neq,
                                  _ptr(Q), _ptr(G), _ptr(A), _ptr(fwd.workspace),
                                  fwd.workspace.numel(), _ptr(dl_dz),
@@ -185,7 +193,7 @@ def qp_backward(fwd: ForwardResult, dl_dz: torch.Tensor, *, dl_dlam=None, dl_dnu
             rc = lib.qp_backward_ext(ctypes.byref(opts), _dtype_code(Q), B, n, nineq, neq,
                                      _ptr(Q), _ptr(G), _ptr(A), _ptr(fwd.workspace),
                                      fwd.workspace.numel(), _ptr(dl_dz), _ptr(extra[0]),
-                                     _ptr(extra[1]), *[_ptr(g) for g in grads],
+                                     _ptr(extra[1]), *[_ptr(g) for g in grads], _ptr(status),
                                      _stream_handle(dev))
     _check(rc)
     return tuple(grads)

@@ -159,6 +159,7 @@ class QPServer:
         self.queues = [collections.deque() for _ in range(len(self.size_classes) + 1)]
         self.cv = threading.Condition()
         self.inflight = []
+        self.max_inflight_seen = 0   # most batches launched and not yet finished at once
         self.latencies = []
         self.batch_sizes = []
         self.completed = 0
@@ -194,6 +195,7 @@ class QPServer:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
         nb = max(len(self.batch_sizes), 1)
         return {"completed": self.completed, "batches": len(self.batch_sizes),
+                "max_inflight_seen": self.max_inflight_seen,
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
@@ -333,6 +335,7 @@ class QPServer:
                     break
                 sidx = self.free_streams.pop(0)
                 self.inflight.append(self._launch(reqs, sidx))
+                self.max_inflight_seen = max(self.max_inflight_seen, len(self.inflight))
                 self.batch_sizes.append(len(reqs))
                 progressed = True
             if not progressed:

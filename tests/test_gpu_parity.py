@@ -8,7 +8,8 @@ import pytest
 import torch
 
 from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward, supported
-from tests.helpers import grad_floor, kkt_residuals_fp64, oracle_solve_and_grad, rel_err
+from tests.helpers import (grad_floor, kkt_residuals_fp64, oracle_solve_and_grad, rel_err,
+                           rel_err_inf)
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -35,26 +36,33 @@ def _run(batch, g, dtype):
 
 
 def _compare(batch, g, out, idx, ztol, gtol, ltol=None):
+    """Oracle parity of the selected instances in both forms of the relative error: per
+    instance ‖x − x_ref‖₂/max(‖x_ref‖₂, floor) and max_i |x_i − x_ref,i|/max(‖x_ref‖∞, floor).
+    Returns the worst value of each result in each form."""
+    idx = list(idx)
     sols, grads = oracle_solve_and_grad(batch, g, idx)
-    ez = rel_err(out["z"][idx], [s["z"] for s in sols])
-    assert ez.max() <= ztol, ("z", ez.max())
-    if ltol is not None:
-        if batch.nineq:
-            el = rel_err(out["lam"][idx], [s["lam"] for s in sols])
-            assert el.max() <= ltol, ("lam", el.max())
-        if batch.neq:
-            en = rel_err(out["nu"][idx], [s["nu"] for s in sols])
-            assert en.max() <= ltol, ("nu", en.max())
     worst = {}
+    for name, ref_of, tol in (("z", lambda s, gr: s["z"], ztol),
+                              ("lam", lambda s, gr: s["lam"], ltol),
+                              ("nu", lambda s, gr: s["nu"], ltol)):
+        ref = [ref_of(s, None) for s in sols]
+        if tol is None or np.asarray(ref).size == 0:
+            continue
+        for form, fn in (("l2", rel_err), ("inf", rel_err_inf)):
+            e = fn(out[name][idx], ref)
+            worst[(name, form)] = e.max()
+            assert e.max() <= tol, (name, form, e.max(), idx[int(np.argmax(e))])
+    gsel = np.asarray(g)[idx]
+    zref = [s["z"] for s in sols]
     for k in GRAD_NAMES:
         ref = [gr[k] for gr in grads]
         if np.asarray(ref).size == 0:
             continue
-        fl = grad_floor(k, np.asarray(g)[list(idx)], [s["z"] for s in sols])
-        e = rel_err(out[k][idx], ref, fl)
-        worst[k] = e.max()
-        assert e.max() <= gtol, (k, e.max(), np.argmax(e))
-    return ez.max(), worst
+        for form, fn, nrm in (("l2", rel_err, 2), ("inf", rel_err_inf, np.inf)):
+            e = fn(out[k][idx], ref, grad_floor(k, gsel, zref, norm=nrm))
+            worst[(k, form)] = e.max()
+            assert e.max() <= gtol, (k, form, e.max(), idx[int(np.argmax(e))])
+    return worst
 
 
 def test_plain_fp64_config():
@@ -77,9 +85,10 @@ def test_sweep_fp32(n):
     _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
 
 
-def test_full_batch_sampled_and_certified():
+def test_full_batch_oracle_parity_and_certified():
     """The benchmark launch (B = 128, n = 100, 100 inequalities, 50 equalities): every
-    instance passes an FP64 KKT certificate, sampled instances match the oracle."""
+    instance passes an FP64 KKT certificate and matches the oracle on z*, λ*, ν* and all six
+    gradients, in the 2-norm and the ∞-norm forms of the relative error."""
     B, n = 128, 100
     batch = inputs.random_batch(B, n, n, n // 2, workload=inputs.WL_SWEEP, dtype=np.float32)
     g = inputs.upstream_grad(B, n, workload=inputs.WL_SWEEP)
@@ -89,7 +98,9 @@ def test_full_batch_sampled_and_certified():
     # z*, λ*, ν* are rounded to FP32 on output, which bounds what the certificate can show.
     assert cert[:, 0].max() <= 1e-4 and cert[:, 1].max() <= 1e-5
     assert cert[:, 2].max() <= 1e-5 and cert[:, 3].max() <= 0
-    _compare(batch, g, out, [0, 17, 64, 101, 127], 1e-5, 1e-4, ltol=1e-4)
+    worst = _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
+    print("worst relative errors over the 128 instances:",
+          {f"{k}/{f}": f"{v:.2e}" for (k, f), v in worst.items()})
 
 
 def test_onehot_structured():

@@ -1,11 +1,12 @@
 """Serving loop on the GPU: mixed-size requests, continuous batching on several streams;
-each request's result equals the same instance solved alone."""
+each request's result equals the same instance solved alone and matches the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
 
 from paper_1703_00443_gb300 import inputs, qp_backward, qp_forward
 from paper_1703_00443_gb300.serving import QPServer, request_bytes
+from tests.helpers import oracle_many, rel_err, rel_err_inf
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -32,22 +33,38 @@ def _alone(data, g):
     return out
 
 
-def test_served_results_equal_alone_and_batches_overlap():
-    sizes = inputs.serve_sizes(40, n_hi=256)
+def test_served_results_equal_alone_match_oracle_and_batches_overlap():
+    # mixed sizes, including instances on the global-memory kernel path (n >= 200)
+    sizes = inputs.serve_sizes(40, n_hi=256) + [(200, 200, 50), (256, 256, 64), (230, 230, 57)]
     pool = _pool(sizes)
     server = QPServer(device=DEV, max_inflight=3, max_batch=8)
     try:
         futs = [server.submit(*data, g) for data, g in pool]
-        results = [f.result(timeout=120) for f in futs]
+        results = [f.result(timeout=300) for f in futs]
     finally:
         server.close()
     st = server.stats()
     assert st["completed"] == len(pool) and st["batches"] >= 5   # batch cap forces several
-    for (data, g), res in zip(pool, results):
+    assert st["max_inflight_seen"] >= 2          # a batch was launched while another ran
+    refs = oracle_many([tuple(np.float64(x) for x in data) + (np.float64(g),) for data, g in pool])
+    for i, ((data, g), res) in enumerate(zip(pool, results)):
         assert res["status"] == 0
-        ref = _alone(data, g)
-        for k in ref:
-            assert np.array_equal(res[k], ref[k]), k
+        alone = _alone(data, g)
+        for k in alone:
+            assert np.array_equal(res[k], alone[k]), k
+        sol, gr = refs[i]
+        gn = np.linalg.norm(np.float64(g))
+        for k, ref, tol in (("z", sol["z"], 1e-5), ("lam", sol["lam"], 1e-4),
+                            ("nu", sol["nu"], 1e-4)) + tuple((k, gr[k], 1e-4) for k in NAMES):
+            if ref.size == 0:
+                continue
+            fl = 1e-12
+            if k.startswith("d"):
+                fl = 1e-3 * gn * (max(1.0, np.linalg.norm(sol["z"])) if k in ("dQ", "dG", "dA") else 1.0)
+            x = np.float64(res[k]).reshape(1, -1)
+            e2 = rel_err(x, ref.reshape(1, -1), fl)[0]
+            ei = rel_err_inf(x, ref.reshape(1, -1), fl)[0]
+            assert e2 <= tol and ei <= tol, (i, sizes[i], k, e2, ei)
 
 
 def test_hbm_budget_admission_and_rejection():
