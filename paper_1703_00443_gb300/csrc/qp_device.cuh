@@ -15,8 +15,9 @@
 // where RE = [G 0]·S = [GP, GT] (nineq × (n+neq)) and M = G P Gᵀ.  S, RE and M are
 // produced together, once per solve, by a symmetric Gauss-Jordan sweep over the first
 // n+neq pivots of [[K11, [G 0]ᵀ], [[G 0], 0]] held in registers (4×4 tiles per thread).
-// Each iteration factors M + D(s/λ) = L Lᵀ by a right-looking Cholesky that also forms
-// X = L⁻¹ in the same column loop, so every triangular solve is a product with X or Xᵀ.
+// Each iteration factors M + D(s/λ) = L Lᵀ by a right-looking Cholesky in 4×4 register
+// tiles that forms X = L⁻¹ in the same loop (chol_blk with FULLX), so every triangular solve
+// is a product with X or Xᵀ (chol_solve).
 //
 // Precision.  T is the matrix/factor type (float or double).  The iterate (z, s, λ, ν)
 // is kept in FP64, and the KKT residual vectors and the backward refinement residual are
@@ -37,6 +38,9 @@ namespace qpk {
 
 constexpr int NTHREADS = 512;
 constexpr int NWARPS = NTHREADS / 32;
+// Scratch elements blk_solve needs: the block's right-hand side, per-warp partial sums and
+// the staged inverse diagonal block (32 × 33).
+constexpr int BLK_SOLVE_SCR = 32 + 32 * NWARPS + 32 * 33;
 // Shared-memory budget (bytes) under which the global-memory path keeps its Cholesky panels
 // in shared memory; below every supported device's opt-in limit of the target (227 KB).
 constexpr size_t LARGE_PANEL_SMEM_CAP = 200 * 1024;
@@ -47,8 +51,9 @@ __host__ __device__ constexpr int chol_nb(int esz) { return esz == 4 ? 32 : 16; 
 // (4×4 tiles of the lower triangle in at most two register slots per thread).
 constexpr int REG_CHOL_MAX_P = 176;
 // Whether the global-memory path factors a p×p Schur complement with the register-tile
-// Cholesky (X = L⁻¹ in Mb, solves by two products) rather than the blocked routine (blocked L
-// with inverted diagonal blocks in Mb, solves by block substitution).
+// Cholesky (chol_blk with FULLX: X = L⁻¹ in Mb, solves by two products) rather than the
+// blocked routine (gchol_factor: L with inverted 32×32 (16×16 in FP64) diagonal blocks in
+// Mb, solved by block substitution, blk_solve).
 __host__ __device__ inline bool reg_chol_ok(int p, int esz) {
   const int NT = (p + 3) >> 2, nt = NT * (NT + 1) / 2;
   return nt <= NTHREADS || (esz == 4 && nt <= 2 * NTHREADS && p <= REG_CHOL_MAX_P);
@@ -82,8 +87,9 @@ __host__ __device__ inline int padded_nz(int n, int m) { return n + ((4 - (n + m
 // ------------------------------------------------------------------ layouts
 // Per-instance workspace (global memory) kept from forward to backward.
 // Layout shared by both kernel paths (the backward pass reads only this prefix):
-// SR = [S; RE] ((m1+p) × m1, m1 = nz + neq), the p×p block with X = L⁻¹ (lower) and M
-// (strict upper), the FP64 iterate (z, s, λ, ν) and the stamp: eight int32 words
+// SR = [S; RE] ((m1+p) × m1, m1 = nz + neq), the p×p block with the factor of M + D(s/λ)
+// (lower triangle: X = L⁻¹, or for large p on the global path L with inverted diagonal
+// blocks) and M (strict upper), the FP64 iterate (z, s, λ, ν) and the stamp: eight int32 words
 // {status code | flags, STAMP_MAGIC, n, nineq, neq, element size | path << 8, nz,
 // stamp_hash(Q, G, A)} that the backward pass checks before it trusts the rest.  The global-memory
 // path appends diag(M), its Cholesky work matrix (row stride round4(p)) and its panel
@@ -122,7 +128,7 @@ struct FwdSmem {
     m1 = nz + m;
     N3 = m1 + p;
     ldS = m1;
-    ldM = p > 0 ? p : 1;
+    ldM = p > 0 ? (p + 3) / 4 * 4 : 1;   // rows of M/X on 16-byte boundaries
     NT3 = (N3 + 3) / 4;
     NTp = (p + 3) / 4;
     const size_t es = sizeof(T);
@@ -142,6 +148,7 @@ struct FwdSmem {
         size_t a = 2 * (32 * (size_t)NT3 + 16), b = 2 * (32 * (size_t)NTp + 16);
         c = (a > b ? a : b) * es + 64;
         if (c < 8 * (size_t)NTHREADS) c = 8 * (size_t)NTHREADS;
+        if (c < BLK_SOLVE_SCR * es) c = BLK_SOLVE_SCR * es;
       } else {
         // ≥ the pivot scratch of the large routines, and ≥ the panels of the register-tile
         // Cholesky, which the global-memory path uses while p ≤ REG_CHOL_MAX_P.
@@ -153,9 +160,10 @@ struct FwdSmem {
       cbytes = align_up(c, 16);
     }
     pan_smem = span_smem = 0;
+    const size_t p4 = (size_t)(p + 3) / 4 * 4;
     const size_t tail = align_up(8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16) +
                         align_up(8 * ((size_t)n + p + m), 16) +
-                        align_up(es * (3 * (size_t)m1 + 12 * (size_t)p), 16) +
+                        align_up(es * (3 * (size_t)m1 + 12 * p4), 16) +
                         align_up(8 * 4 * NWARPS, 16);
     if (large) {
       // The Cholesky panel and staging buffer (pivot scratch plus 2·chol_nb rows of ld
@@ -178,7 +186,7 @@ struct FwdSmem {
     o += cbytes;
     odbl = o;  o = align_up(o + 8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
-    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 12 * (size_t)p), 16);
+    ovec = o;  o = align_up(o + es * (3 * (size_t)m1 + 12 * p4), 16);
     ored = o;  o = align_up(o + 8 * 4 * NWARPS, 16);
     total = o;
   }
@@ -193,7 +201,7 @@ struct BwdSmem {
     size_t o = 0;
     odbl = o;   o = align_up(o + 8 * (3 * ((size_t)n + p + m) + 2 * (size_t)p), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
-    ovec = o;   o = align_up(o + es * (3 * m1 + 4 * (size_t)p), 16);
+    ovec = o;   o = align_up(o + es * (3 * m1 + 4 * (size_t)(p + 3) / 4 * 4), 16);
     ored = o;   o = align_up(o + 8 * 4 * NWARPS, 16);
     oscr = o;   o = align_up(o + 8 * (size_t)4 * NTHREADS, 16);
     total = o;
@@ -450,13 +458,77 @@ __device__ __forceinline__ void mv_rows(const T* M, int ld, int rows, int cols, 
   }
 }
 
+// y_r = Σ_c M[r·ld + c]·x[c] for r < rows and all c < cols, when M's rows and x start on
+// 16-byte boundaries and cols is a whole number of 16-byte vectors (cols ≤ 8·GL vectors):
+// lane gl of a row's GL lanes keeps x's vectors gl, gl+GL, ... in registers for every row, so
+// each row is read once from shared memory and x once per call.  Returns false (doing
+// nothing) when those conditions do not hold; the caller then uses mv_rows.
+template <int GL, typename T, typename F>
+__device__ __forceinline__ bool mv_rows_xreg(const T* M, int ld, int rows, int cols, const T* x,
+                                             F epi) {
+  constexpr int W = 16 / sizeof(T), XV = 8;
+  const int nv = cols / W;
+  if (cols % W != 0 || ld % W != 0 || nv > XV * GL ||
+      ((((uintptr_t)M) | ((uintptr_t)x)) % 16) != 0)
+    return false;
+  const int tid = threadIdx.x;
+  const int g = tid / GL, gl = tid % GL;
+  constexpr int NG = NTHREADS / GL;
+  T xr[XV][W];
+#pragma unroll
+  for (int k = 0; k < XV; ++k) {
+    const int v = gl + k * GL;
+    if (v < nv) {
+      if constexpr (W == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(x + v * W);
+        xr[k][0] = q.x; xr[k][1] = q.y; xr[k][2] = q.z; xr[k][3] = q.w;
+      } else {
+        const double2 q = *reinterpret_cast<const double2*>(x + v * W);
+        xr[k][0] = q.x; xr[k][1] = q.y;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e) xr[k][e] = T(0);
+    }
+  }
+  for (int r0 = 0; r0 < rows; r0 += NG) {
+    const int r = r0 + g;
+    T acc[2] = {T(0), T(0)};
+    if (r < rows) {
+      const T* row = M + (size_t)r * ld;
+#pragma unroll
+      for (int k = 0; k < XV; ++k) {
+        const int v = gl + k * GL;
+        if (v < nv) {
+          T a[W];
+          if constexpr (W == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(row + v * W);
+            a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+          } else {
+            const double2 q = *reinterpret_cast<const double2*>(row + v * W);
+            a[0] = q.x; a[1] = q.y;
+          }
+#pragma unroll
+          for (int e = 0; e < W; ++e) acc[k & 1] = fma(a[e], xr[k][e], acc[k & 1]);
+        }
+      }
+    }
+    T s = acc[0] + acc[1];
+#pragma unroll
+    for (int off = GL / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (r < rows && gl == 0) epi(r, s);
+  }
+  return true;
+}
+
 // y_c = Σ_r M[r·ld + c]·x[r] for c < cols, over all r (TRI_ALL), r ≥ c (TRI_LOWER) or
 // r < c (TRI_SUPPER).  Row ranges are split over the threads that share a column; partial
 // sums meet in `scr` (NTHREADS entries).  Ends with a barrier, so epi's writes are visible
 // on return.
 template <typename T, typename F>
 __device__ __forceinline__ void mv_cols(const T* M, int ld, int rows, int cols, int tri,
-                                        const T* x, T* scr, F epi) {
+                                        const T* x, T* scr, F epi, int cap = NTHREADS) {
+  (void)cap;
   const int tid = threadIdx.x;
   if (cols <= 0) return;
   if (cols > NTHREADS / 2) {
@@ -635,6 +707,102 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restri
     Acc<T> acc = scr[j];
     for (int q = 1; q < nparts; ++q) acc.merge(scr[q * 4 * nq + j]);
     out_z[j] = acc.value() + add_z(j);
+  }
+  __syncthreads();
+}
+
+// The leading part of a split value: the FP32 rounding for T = float, the value itself for
+// T = double.
+__device__ __forceinline__ float split_hi(float2 v) { return v.x; }
+__device__ __forceinline__ double split_hi(double v) { return v; }
+
+// kkt_apply in plain T arithmetic (one FMA per matrix element, x rounded to T): the same
+// operator and the same quad/partial-sum organisation, with an error of order
+// n·2⁻²⁴·Σ|terms| for T = float instead of 2⁻⁴⁸.  The interior point loop uses it while μ
+// is far above its tolerance, where that error is far below what the step needs.
+template <typename T, typename FZ, typename FL, typename FN>
+__device__ __forceinline__ void kkt_apply_fast(int n, int p, int m, const T* __restrict__ Q,
+                                               const T* __restrict__ G, const T* __restrict__ A,
+                                               const typename Split<T>::V* xv, T* scr, int kscr,
+                                               FZ add_z, FL add_l, FN add_n,
+                                               double* out_z, double* out_l, double* out_n) {
+  const int tid = threadIdx.x;
+  const int R = n + p + m;
+  auto rowp = [&](int r) -> const T* {
+    return r < n ? Q + (size_t)r * n : (r < n + p ? G + (size_t)(r - n) * n : A + (size_t)(r - n - p) * n);
+  };
+  const bool vec = (n % 4 == 0) &&
+      ((((uintptr_t)Q) | ((uintptr_t)G) | ((uintptr_t)A)) % (4 * sizeof(T)) == 0);
+  const int nq = (n + 3) / 4;
+  const int nparts = max(1, min(NTHREADS / nq, kscr / (4 * nq)));
+  for (int t = tid; t < nq * nparts; t += NTHREADS) {
+    const int jq = t % nq, part = t / nq;
+    const int chunk = (R + nparts - 1) / nparts;
+    const int r0 = part * chunk, r1 = min(R, r0 + chunk);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    int r = r0;
+    for (; r + 4 <= r1; r += 4) {
+      T av[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ldg4_row(av[u], rowp(r + u), 4 * jq, n, vec);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T x = split_hi(xv[r + u]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = fma(av[u][c], x, acc[c]);
+      }
+    }
+    for (; r < r1; ++r) {
+      T av[4];
+      ldg4_row(av, rowp(r), 4 * jq, n, vec);
+      const T x = split_hi(xv[r]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] = fma(av[c], x, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) scr[part * 4 * nq + 4 * jq + c] = acc[c];
+  }
+  {
+    constexpr int GL = 8, NG = NTHREADS / GL, QB = 4;
+    const int g = tid / GL, gl = tid % GL;
+    for (int r0 = 0; r0 < p + m; r0 += 2 * NG) {
+      const int rr[2] = {r0 + g, r0 + NG + g};
+      T acc[2] = {T(0), T(0)};
+      for (int qb0 = 0; qb0 < nq; qb0 += GL * QB) {
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int rw = rr[h2];
+          const T* rowv = (rw < p) ? G + (size_t)rw * n : A + (size_t)(rw - p) * n;
+#pragma unroll
+          for (int u = 0; u < QB; ++u) {
+            const int q = qb0 + gl + u * GL;
+            if (rw < p + m && q < nq) {
+              T av[4];
+              ldg4_row(av, rowv, 4 * q, n, vec);
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (4 * q + c < n) acc[h2] = fma(av[c], split_hi(xv[4 * q + c]), acc[h2]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll
+        for (int off = GL / 2; off > 0; off >>= 1) acc[h2] += __shfl_xor_sync(0xffffffffu, acc[h2], off);
+        const int rw = rr[h2];
+        if (rw < p + m && gl == 0) {
+          if (rw < p) out_l[rw] = (double)acc[h2] + add_l(rw);
+          else out_n[rw - p] = (double)acc[h2] + add_n(rw - p);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += NTHREADS) {
+    T a = scr[j];
+    for (int q = 1; q < nparts; ++q) a += scr[q * 4 * nq + j];
+    out_z[j] = (double)a + add_z(j);
   }
   __syncthreads();
 }
@@ -888,34 +1056,47 @@ __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restric
   return true;
 }
 
-// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ with X = L⁻¹ formed in the same loop
-// (right-looking over 4-column blocks, two barriers per block).  M comes from the strict
-// upper triangle of Mb plus dM; X is written to the lower triangle (with diagonal) of Mb.
-// Block K:  one thread factors the diagonal tile, L_KK = chol(A_KK), and inverts it;
-//           owners form the panel L_IK = A_IK L_KK⁻ᵀ (I > K) and the new block row of X,
-//           X_KJ ← L_KK⁻¹ X_KJ (J ≤ K), and publish both;
-//           every tile updates: A_IJ −= L_IK L_JKᵀ (I ≥ J > K), X_IJ −= L_IK X_KJ (I > K ≥ J).
-// Padding rows/columns beyond p are the identity and never couple to the real ones.
-// Returns false on every thread if a pivot is not positive or not finite.
-template <typename T, int CH>
-__device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const T* dsh, T* cb) {
-  const int tid = threadIdx.x;
+// Blocked Cholesky factorisation M + D(dsh) = L Lᵀ in 4×4 register tiles (right-looking over
+// 4-column steps, two barriers per step).  M comes from the strict upper triangle of Mb plus
+// dM.  The factor is left in the lower triangle of Mb in the blocked form blk_solve applies:
+// L's tiles below the NB×NB diagonal blocks (NB = chol_nb, 32 in FP32 and 16 in FP64) as they
+// are, and on each diagonal block its inverse L_BB⁻¹ (lower triangular).  Step K:
+//   A: one thread factors the diagonal tile, L_KK = chol(A_KK), and inverts it, V_K = L_KK⁻¹;
+//   B: owners form the panel L_IK = A_IK V_Kᵀ (I > K) and the finished block row of the
+//      block inverse, X_KJ ← V_K X_KJ (J in K's diagonal block), and publish both;
+//   C: A_IJ −= L_IK L_JKᵀ (I ≥ J > K) and, inside K's diagonal block, X_IJ −= L_IK X_KJ.
+// The inverse tiles X are owned by threads counted down from the last one, so on most sizes
+// they fall on threads without a trailing tile and cost no extra pass.  The owner of the next
+// diagonal tile factors it right after its own update.  Padding rows/columns beyond p are the
+// identity and never couple to the real ones.  Returns false on every thread if a pivot is
+// not positive or not finite.
+template <typename T, int CH, bool FULLX = false>
+__device__ __noinline__ bool chol_blk(int p, T* Mb, int ldM, const T* dM, const T* dsh, T* cb) {
+  // FULLX: the "diagonal block" is the whole matrix, so X = L⁻¹ in full replaces L.
   const int NT = (p + 3) >> 2, ntiles = NT * (NT + 1) / 2;
-  if (ntiles > CH * NTHREADS) return false;   // register tiles too few (host plans avoid it)
-  // cb layout per parity: L panel [16·NT], X block row [16·NT], Linv [16]; flags after.
+  const int TB = FULLX ? NT : chol_nb((int)sizeof(T)) / 4;   // tiles along a diagonal block
+  const int TBT = TB * (TB + 1) / 2;                          // tiles in a full block's lower triangle
+  const int tid = threadIdx.x;
+  const int nfull = NT / TB, tlast = NT - nfull * TB;
+  const int nxt = nfull * TBT + tlast * (tlast + 1) / 2;
+  if (ntiles > CH * NTHREADS || nxt > CH * NTHREADS) return false;   // host plans avoid it
+  // cb layout per parity: L panel [16·NT], X block row [16·NT], V_K [16]; flags after both.
   const int pstride = 32 * NT + 16;
   int* flag = reinterpret_cast<int*>(cb + 2 * pstride);
-  // A tiles are owned column-major (a tile column, i.e. a panel, sits in one or two warps);
-  // X tiles row-major (a block row of X likewise).
   T a[CH][16], x[CH][16];
   int tI[CH], tJ[CH], xI[CH], xJ[CH];
 #pragma unroll
   for (int s = 0; s < CH; ++s) {
     const int t = tid + s * NTHREADS;
     int I = -1, J = 0, XI = -1, XJ = 0;
-    if (t < ntiles) {
-      tile_of_colmajor(t, NT, I, J);
-      tile_of(t, XI, XJ);
+    if (t < ntiles) tile_of_colmajor(t, NT, I, J);
+    const int u = (NTHREADS - 1 - tid) + s * NTHREADS;   // inverse tiles from the top thread
+    if (u < nxt) {
+      const int b = u / TBT;
+      int i, j;
+      tile_of(u - b * TBT, i, j);
+      XI = b * TB + i;
+      XJ = b * TB + j;
     }
     tI[s] = I;
     tJ[s] = J;
@@ -966,10 +1147,7 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
             for (int q = 0; q < c; ++q) v = fma(-l[r * 4 + q], l[c * 4 + q], v);
             l[r * 4 + c] = v * inv;
           }
-#pragma unroll
-          for (int q = c + 1; q < 4; ++q) l[c * 4 + q] = T(0);
         }
-        // V = L_KK⁻¹ (lower triangular), by forward substitution on the identity.
         T v[16];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -981,18 +1159,26 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
             for (int q = c; q < r; ++q) acc = fma(-l[r * 4 + q], v[q * 4 + c], acc);
             v[r * 4 + c] = acc * li[r];
           }
-        st16(Vb, v);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) st4(Vb + 4 * r, v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
         flag[K & 1] = good ? 0 : 1;
       }
     }
     __syncthreads();
     if (flag[K & 1]) return false;
-    // Phase B: panel L_IK = A_IK Vᵀ and block row X_KJ ← V X_KJ.
+    T V[16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      T row4[4];
+      ld4(row4, Vb + 4 * r);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) V[r * 4 + q] = row4[q];
+    }
+    // Phase B: panel L_IK = A_IK V_Kᵀ (V_K lower: column c needs q ≤ c), and block row K of
+    // the diagonal block's inverse.
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       if (tJ[s] == K && tI[s] > K) {
-        T V[16];
-        ld16(V, Vb);
         T Ln[16];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -1000,14 +1186,14 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
           for (int c = 0; c < 4; ++c) {
             T acc = T(0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc = fma(a[s][r * 4 + q], V[c * 4 + q], acc);
+            for (int q = 0; q <= c; ++q) acc = fma(a[s][r * 4 + q], V[c * 4 + q], acc);
             Ln[r * 4 + c] = acc;
           }
         st_panel(Lb, 4 * NT, tI[s], Ln);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) a[s][e] = Ln[e];
       }
       if (xI[s] == K) {
-        T V[16];
-        ld16(V, Vb);
         T Xn[16];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -1015,7 +1201,7 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
           for (int c = 0; c < 4; ++c) {
             T acc = T(0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc = fma(V[r * 4 + q], x[s][q * 4 + c], acc);
+            for (int q = 0; q <= r; ++q) acc = fma(V[r * 4 + q], x[s][q * 4 + c], acc);
             Xn[r * 4 + c] = acc;
           }
 #pragma unroll
@@ -1029,7 +1215,7 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
       }
     }
     __syncthreads();
-    // Phase C: trailing update of A and of the rows of X below block K.
+    // Phase C: trailing update, and the block inverse's rows below K in K's block.
 #pragma unroll
     for (int s = 0; s < CH; ++s) {
       const int I = tI[s], J = tJ[s];
@@ -1064,23 +1250,36 @@ __device__ __noinline__ bool chol_inv(int p, T* Mb, int ldM, const T* dM, const 
       }
     }
   }
+  // L below the diagonal blocks, the block inverses on them.
 #pragma unroll
   for (int s = 0; s < CH; ++s) {
-    const int I = xI[s], J = xJ[s];
-    if (I < 0) continue;
+    const int I = tI[s], J = tJ[s];
+    if (I >= 0 && I / TB != J / TB) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = 4 * I + r, j = 4 * J + q;
-        if (i < p && j <= i) Mb[(size_t)i * ldM + j] = x[s][r * 4 + q];
-      }
+        for (int q = 0; q < 4; ++q) {
+          const int i = 4 * I + r, j = 4 * J + q;
+          if (i < p && j < p) Mb[(size_t)i * ldM + j] = a[s][r * 4 + q];
+        }
+    }
+    const int XI = xI[s], XJ = xJ[s];
+    if (XI >= 0) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = 4 * XI + r, j = 4 * XJ + q;
+          if (i < p && j <= i) Mb[(size_t)i * ldM + j] = x[s][r * 4 + q];
+        }
+    }
   }
   __syncthreads();
   return true;
 }
 
-// out = Xᵀ(X·rhs) = (M + D)⁻¹ rhs with X = L⁻¹ in the lower triangle of Mb.
+// out = Xᵀ(X·rhs) = (M + D)⁻¹ rhs with X = L⁻¹ in the lower triangle of Mb (chol_blk with
+// FULLX).
 template <typename T>
 __device__ __forceinline__ void chol_solve(int p, const T* Mb, int ldM, const T* rhs, T* y,
                                            T* out, T* scr) {
@@ -1092,10 +1291,21 @@ __device__ __forceinline__ void chol_solve(int p, const T* Mb, int ldM, const T*
 // out = M·x with M symmetric, stored as its strict upper triangle in Mb plus diag in dM.
 template <typename T>
 __device__ __forceinline__ void mv_sym_upper(int p, const T* Mb, int ldM, const T* dM,
-                                             const T* x, T* tmp, T* out, T* scr) {
+                                             const T* x, T* tmp, T* out, T* scr,
+                                             int cap = NTHREADS) {
   mv_rows<8>(Mb, ldM, p, p, TRI_SUPPER, x, [&](int r, T v) { tmp[r] = fma(dM[r], x[r], v); });
   __syncthreads();
-  mv_cols(Mb, ldM, p, p, TRI_SUPPER, x, scr, [&](int c, T v) { out[c] = tmp[c] + v; });
+  mv_cols(Mb, ldM, p, p, TRI_SUPPER, x, scr, [&](int c, T v) { out[c] = tmp[c] + v; }, cap);
+}
+
+// Ask L2 to fetch [ptr, ptr + bytes) (128-byte lines, spread over the block's threads), so
+// that later phases find the data there instead of waiting for DRAM one dependent phase at a
+// time.  No result depends on it.
+__device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
+  if (!ptr) return;
+  const char* c = static_cast<const char*>(ptr);
+  for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)NTHREADS * 128)
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(c + o));
 }
 
 // Nanoseconds of the GPU's global timer.
@@ -1129,7 +1339,7 @@ namespace qpk {
 // they are copied there for the backward pass.
 template <typename T, typename FS, typename FF, typename FV>
 __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& L,
-                                         unsigned char* sm, T* SR, T* Mb, T* dM,
+                                         unsigned char* sm, T* SR, T* Mb, int ldMb, T* dM,
                                          bool ws_resident, FS setup, FF factor, FV solve) {
   using V = typename Split<T>::V;
   const int tid = threadIdx.x;
@@ -1142,14 +1352,16 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
   double *qd = rn + m, *hd = qd + n, *bd = hd + p;   // q, h, b (constant over the solve)
   V* xs = reinterpret_cast<V*>(sm + L.osplit);
   T* tv = reinterpret_cast<T*>(sm + L.ovec);
-  T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *dla = dl + p;
-  T *rhs = dla + p, *rhsa = rhs + p, *dsh = rhsa + p, *mdl = dsh + p, *tmp = mdl + p;
-  T *dsv = tmp + p, *ccv = dsv + p;
+  const int p4 = (p + 3) / 4 * 4;   // vector strides keep every vector 16-byte aligned
+  T *u = tv, *wv = u + m1, *dzn = wv + m1 + p4, *y = dzn + m1, *dl = y + p4, *dla = dl + p4;
+  T *rhs = dla + p4, *rhsa = rhs + p4, *dsh = rhsa + p4, *mdl = dsh + p4, *tmp = mdl + p4;
+  T *dsv = tmp + p4, *ccv = dsv + p4;
   float* red = reinterpret_cast<float*>(sm + L.ored);
   double* dred = reinterpret_cast<double*>(sm + L.ored);
   Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.ocb);
   T* tscr = reinterpret_cast<T*>(sm + L.ocb);
   const int kscr = (int)(L.cbytes / sizeof(Acc<T>));
+  const int tcap = (int)(L.cbytes / sizeof(T));   // T elements of the work region
   (void)cb;
   __shared__ int s_timeout;
   const unsigned long long t_start = P.time_limit_ns ? globaltimer_ns() : 0ull;
@@ -1167,7 +1379,7 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
   T* wX = reinterpret_cast<T*>(wsb + W.oX);
   double* wIt = reinterpret_cast<double*>(wsb + W.oIt);
   int32_t* wSt = reinterpret_cast<int32_t*>(wsb + W.oSt);
-  const int ldS = m1, ldM = p > 0 ? p : 1;
+  const int ldS = m1, ldM = ldMb;
 
   int status = ST_CONV, it = 0, extra = 0, flags = 0;
   float last[4] = {0.f, 0.f, 0.f, 0.f};   // residual norms and μ at the returned iterate
@@ -1264,13 +1476,14 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
     ok = factor(dsh);
     if (!ok) status = ST_NOTPD;
     if (ok) {
-      mv_rows<8>(SR, ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
+      if (!mv_rows_xreg<8>(SR, ldS, m1 + p, m1, u, [&](int r, T val) { wv[r] = val; }))
+        mv_rows<8>(SR, ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
       __syncthreads();
       for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] - hb[i];
       __syncthreads();
       solve(rhs, y, dl, tscr);
       mv_cols(SR + (size_t)m1 * ldS, ldS, p, m1, TRI_ALL, dl, tscr,
-              [&](int c, T val) { dzn[c] = wv[c] - val; });
+              [&](int c, T val) { dzn[c] = wv[c] - val; }, tcap);
       float v[4] = {-INFINITY, 0.f, -INFINITY, 0.f};
       for (int i = tid; i < n; i += NTHREADS) z[i] = (double)dzn[i];
       for (int i = tid; i < m; i += NTHREADS) nu[i] = (double)dzn[nz + i];
@@ -1295,6 +1508,35 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
       float lam_max = 0.f, lam_check = INFINITY;   // ‖λ‖∞ and the level that triggers a
                                                     // certificate check (1e3 × its first value)
       bool loop_notpd = false;                      // a Newton step's factorisation failed
+      // Residual precision (FP32 factors only): the plain FP32 operator while the previous
+      // iteration's μ is above 1e5·mu_tol, the FP64-accurate one from then on.  Convergence
+      // is only ever declared on an FP64-accurate residual.
+      bool exact = sizeof(T) == 8;
+      float mu_prev = INFINITY;
+      // The KKT residual at the current iterate and its norms (v[0..2]) and μ·p (v[3]).
+      auto residual = [&](bool fast, float (&v)[4]) {
+        for (int i = tid; i < n + p + m; i += NTHREADS)
+          xs[i] = Split<T>::make(i < n ? z[i] : (i < n + p ? lam[i - n] : nu[i - n - p]));
+        __syncthreads();
+        if (fast)
+          kkt_apply_fast<T>(n, p, m, Qb, Gb, Ab, xs, tscr, tcap,
+                            [&](int j) { return qd[j]; },
+                            [&](int i) { return s[i] - hd[i]; },
+                            [&](int i) { return -bd[i]; }, rz, rl, rn);
+        else
+          kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, kscr,
+                       [&](int j) { return qd[j]; },
+                       [&](int i) { return s[i] - hd[i]; },
+                       [&](int i) { return -bd[i]; }, rz, rl, rn);
+        v[0] = v[1] = v[2] = v[3] = 0.f;
+        for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
+        for (int i = tid; i < p; i += NTHREADS) {
+          v[1] = ropf<R_MAX>(v[1], fabsf((float)rl[i]));
+          v[3] += (float)s[i] * (float)lam[i];
+        }
+        for (int i = tid; i < m; i += NTHREADS) v[2] = ropf<R_MAX>(v[2], fabsf((float)rn[i]));
+        block_reduce4f<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
+      };
       for (it = 0;; ++it) {
         if (lam_max > lam_check) {
           if (infeasible_cert()) {
@@ -1303,22 +1545,15 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
           }
           lam_check *= 1e3f;
         }
-        for (int i = tid; i < n + p + m; i += NTHREADS)
-          xs[i] = Split<T>::make(i < n ? z[i] : (i < n + p ? lam[i - n] : nu[i - n - p]));
-        __syncthreads();
-        kkt_apply<T>(n, p, m, Qb, Gb, Ab, xs, ascr, kscr,
-                     [&](int j) { return qd[j]; },
-                     [&](int i) { return s[i] - hd[i]; },
-                     [&](int i) { return -bd[i]; }, rz, rl, rn);
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int i = tid; i < n; i += NTHREADS) v[0] = ropf<R_MAX>(v[0], fabsf((float)rz[i]));
-        for (int i = tid; i < p; i += NTHREADS) {
-          v[1] = ropf<R_MAX>(v[1], fabsf((float)rl[i]));
-          v[3] += (float)s[i] * (float)lam[i];
+        if (!exact && mu_prev <= 1e5f * mutol) exact = true;
+        float v[4];
+        residual(!exact, v);
+        if (!exact && v[0] <= tz && v[1] <= tl && v[2] <= tn && v[3] / (float)p <= mutol) {
+          exact = true;             // the stopping test is only taken on the exact residual
+          residual(false, v);
         }
-        for (int i = tid; i < m; i += NTHREADS) v[2] = ropf<R_MAX>(v[2], fabsf((float)rn[i]));
-        block_reduce4f<R_MAX, R_MAX, R_MAX, R_SUM>(v, red);
         const float mu = v[3] / (float)p;
+        mu_prev = mu;
         last[0] = v[0];
         last[1] = v[1];
         last[2] = v[2];
@@ -1375,12 +1610,13 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
           break;
         }
         // Affine-scaling (predictor) direction, Eq. 9.
-        mv_rows<8>(SR, ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
+        if (!mv_rows_xreg<8>(SR, ldS, m1 + p, m1, u, [&](int r, T val) { wv[r] = val; }))
+          mv_rows<8>(SR, ldS, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
         __syncthreads();
         for (int i = tid; i < p; i += NTHREADS) rhsa[i] = wv[m1 + i] + (T)(rl[i] - s[i]);
         __syncthreads();
         solve(rhsa, y, dla, tscr);
-        mv_sym_upper(p, Mb, ldM, dM, dla, tmp, mdl, tscr);
+        mv_sym_upper(p, Mb, ldM, dM, dla, tmp, mdl, tscr, tcap);
         // Δs from the complementarity row where s ≤ λ and from the primal row
         // GΔz + Δs = −r_λ (with GΔz = RE·u − MΔλ) elsewhere: the first multiplies the
         // FP32 error of Δλ by s/λ, which is large exactly where the second is safe.
@@ -1415,8 +1651,8 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
         __syncthreads();
         solve(rhs, y, dl, tscr);
         mv_cols(SR + (size_t)m1 * ldS, ldS, p, m1, TRI_ALL, dl, tscr,
-                [&](int c, T val) { dzn[c] = wv[c] - val; });
-        mv_sym_upper(p, Mb, ldM, dM, dl, tmp, mdl, tscr);
+                [&](int c, T val) { dzn[c] = wv[c] - val; }, tcap);
+        mv_sym_upper(p, Mb, ldM, dM, dl, tmp, mdl, tscr, tcap);
         float w6[4] = {INFINITY, 0.f, 0.f, 0.f};
         for (int i = tid; i < p; i += NTHREADS) {
           const T si = (T)s[i], li = (T)lam[i], d = dl[i];
@@ -1482,7 +1718,7 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
     wIt[n + 2 * p + i] = v;
   }
   if (!bad && !ws_resident)
-    for (int i = tid; i < p * p; i += NTHREADS) wX[i] = Mb[i];
+    for (int i = tid; i < p * p; i += NTHREADS) wX[i] = Mb[(size_t)(i / p) * ldM + i % p];
   if (tid == 0) {
     wSt[0] = status | flags;
     wSt[1] = STAMP_MAGIC;
@@ -1537,11 +1773,12 @@ __device__ __forceinline__ void fwd_smem_path(const FwdInst<T>& I, unsigned char
   T* dM = reinterpret_cast<T*>(sm + L.odM);
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
   const int n = I.n, p = I.p, m = I.m;
-  fwd_body<T>(I, L, sm, SR, Mb, dM, false,
+  const int tcap = (int)(L.cbytes / sizeof(T));
+  fwd_body<T>(I, L, sm, SR, Mb, L.ldM, dM, false,
       [&](const T* Qb, const T* Ab, const T* Gb) {
         return sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
       },
-      [&](const T* dsh) { return chol_inv<T, CH>(p, Mb, L.ldM, dM, dsh, cb); },
+      [&](const T* dsh) { return chol_blk<T, CH, true>(p, Mb, L.ldM, dM, dsh, cb); },
       [&](const T* rhs, T* y, T* out, T* scr) { chol_solve(p, Mb, L.ldM, rhs, y, out, scr); });
 }
 
@@ -1559,7 +1796,8 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
   T* Aw = reinterpret_cast<T*>(I.ws + W.oAw);
   T* pan = reinterpret_cast<T*>(I.ws + W.oPan);
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
-  fwd_body<T>(I, L, sm, SR, Mb, dM, true,
+  const int tcap = (int)(L.cbytes / sizeof(T));
+  fwd_body<T>(I, L, sm, SR, Mb, p > 0 ? p : 1, dM, true,
       [&](const T* Qb, const T* Ab, const T* Gb) {
         return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, L.span_smem != 0, cb);
       },
@@ -1567,9 +1805,9 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
         // Small Schur complements: the register-tile routine (M read from and X written to
         // the workspace, panels in shared memory); otherwise the blocked global routine.
         const int NT = (p + 3) >> 2, nt = NT * (NT + 1) / 2, ldM = p > 0 ? p : 1;
-        if (nt <= NTHREADS) return chol_inv<T, 1>(p, Mb, ldM, dM, dsh, cb);
+        if (nt <= NTHREADS) return chol_blk<T, 1, true>(p, Mb, ldM, dM, dsh, cb);
         if constexpr (sizeof(T) == 4) {
-          if (reg_chol_ok(p, 4)) return chol_inv<T, 2>(p, Mb, ldM, dM, dsh, cb);
+          if (reg_chol_ok(p, 4)) return chol_blk<T, 2, true>(p, Mb, ldM, dM, dsh, cb);
         }
         return gchol_factor<T>(p, Mb, dM, dsh, Aw, pan, L.pan_smem != 0, cb);
       },
@@ -1658,9 +1896,11 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   double *rz = dnu + m, *rl = rz + n, *rn = rl + p;
   V* xs = reinterpret_cast<V*>(sm + L.osplit);
   T* tv = reinterpret_cast<T*>(sm + L.ovec);
-  T *u = tv, *wv = u + m1, *dzn = wv + m1 + p, *y = dzn + m1, *dl = y + p, *rhs = dl + p;
+  const int p4 = (p + 3) / 4 * 4;   // vector strides keep every vector 16-byte aligned
+  T *u = tv, *wv = u + m1, *dzn = wv + m1 + p4, *y = dzn + m1, *dl = y + p4, *rhs = dl + p4;
   Acc<T>* ascr = reinterpret_cast<Acc<T>*>(sm + L.oscr);
   T* tscr = reinterpret_cast<T*>(sm + L.oscr);
+  const int tcap = (int)(8 * 4 * NTHREADS / sizeof(T));   // T elements of the scratch
   float* red = reinterpret_cast<float*>(sm + L.ored);
 
   WsLayout W;
@@ -1695,6 +1935,11 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[i] = qn;
     return;
   }
+  // Everything read below: S/RE and the factor (workspace), Q, G, A (refinement residual).
+  prefetch_l2(X, (size_t)p * p * sizeof(T));
+  prefetch_l2(Qb, (size_t)n * n * sizeof(T));
+  prefetch_l2(Gb, (size_t)p * n * sizeof(T));
+  prefetch_l2(Ab, (size_t)m * n * sizeof(T));
   for (int i = tid; i < n + 2 * p + m; i += NTHREADS) dv[i] = wIt[i];
   for (int i = tid; i < m1; i += NTHREADS)
     u[i] = (i < n) ? -gz[i] : ((i >= nz && gn) ? -gn[i - nz] : T(0));
@@ -1703,7 +1948,8 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   // K_sym [d_z; d_s; d̃_λ; d_ν] = [−∂ℓ/∂z; 0; −∂ℓ/∂λ; −∂ℓ/∂ν]  (Eq. 11; the last two blocks
   // are zero for a loss of z* alone), reduced form:
   //   (M + D(s/λ)) d̃_λ = RE·u + ∂ℓ/∂λ,  [d_z; d_ν] = S·u − REᵀ d̃_λ,  u = [−∂ℓ/∂z; −∂ℓ/∂ν].
-  mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
+  if (!mv_rows_xreg<8>(SR, m1, m1 + p, m1, u, [&](int r, T val) { wv[r] = val; }))
+    mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
   __syncthreads();
   const T* rhs0 = wv + m1;
   if (gl) {
@@ -1711,14 +1957,14 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     __syncthreads();
     rhs0 = rhs;
   }
-  // The global-memory path leaves a blocked factor instead of X for large p.
+  // The global-memory path leaves the blocked factor instead of X = L⁻¹ for large p.
   const bool blk = P.large && !reg_chol_ok(p, (int)sizeof(T));
   if (p > 0) {
     if (blk) blk_solve(p, X, p, rhs0, y, dl, tscr);
     else chol_solve(p, X, p, rhs0, y, dl, tscr);
   }
   mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
-          [&](int c, T val) { dzn[c] = wv[c] - val; });
+          [&](int c, T val) { dzn[c] = wv[c] - val; }, tcap);
   if (p == 0)
     for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
   __syncthreads();
@@ -1754,7 +2000,8 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
                  rz, rl, rn);
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
     __syncthreads();
-    mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
+    if (!mv_rows_xreg<8>(SR, m1, m1 + p, m1, u, [&](int r, T val) { wv[r] = val; }))
+      mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
     __syncthreads();
     for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] + (T)rl[i];
     __syncthreads();
@@ -1763,7 +2010,7 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
       else chol_solve(p, X, p, rhs, y, dl, tscr);
     }
     mv_cols(SR + (size_t)m1 * m1, m1, p, m1, TRI_ALL, dl, tscr,
-            [&](int c, T val) { dzn[c] = wv[c] - val; });
+            [&](int c, T val) { dzn[c] = wv[c] - val; }, tcap);
     if (p == 0)
       for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
     __syncthreads();

@@ -1,7 +1,7 @@
 // qp_large.cuh -- factorisation routines of the global-memory path, used when the KKT blocks
 // of an instance do not fit in shared memory.  Same method and same results layout as the
 // register-tile routines in qp_device.cuh (S and RE in SR, M in the strict upper triangle of
-// Mb plus dM, X = L⁻¹ in the lower triangle of Mb), but the matrices live in the instance's
+// Mb plus dM, the Cholesky factor in the lower triangle of Mb), but the matrices live in the instance's
 // global workspace (L2-resident during the solve).  Pivots are taken in blocks: one warp
 // handles the pivot block, all threads then form the panel and apply the rank-block update
 // to the trailing matrix (LNB = 16 columns per block in the setup sweep, chol_nb columns in
@@ -451,7 +451,7 @@ __device__ __noinline__ bool gchol_factor(int p, T* Mb, const T* dM, const T* ds
   return true;
 }
 
-// out = (L Lᵀ)⁻¹ rhs with the factor of gchol_factor in the lower triangle of Mb (inverted
+// out = (L Lᵀ)⁻¹ rhs with the factor of gchol_factor or chol_blk in the lower triangle of Mb (inverted
 // diagonal blocks V_K, panels L_IK below them); y receives L⁻¹ rhs.  Forward substitution
 // y_K = V_K (rhs_K − Σ_{J<K} L_KJ y_J) by block rows, then back substitution
 // out_K = V_Kᵀ (y_K − Σ_{I>K} L_IKᵀ out_I) by block columns, two barriers per block each way.
@@ -459,7 +459,6 @@ __device__ __noinline__ bool gchol_factor(int p, T* Mb, const T* dM, const T* ds
 // stride NB + 1) together with its partial-sum loads, eight at a time, so the step waits for
 // memory about once.  `scr` holds BLK_SOLVE_SCR elements; y, out and scr are shared memory;
 // ends with a barrier.
-constexpr int BLK_SOLVE_SCR = 32 + 32 * NWARPS + 32 * 33;
 static_assert(BLK_SOLVE_SCR * 8 <= 8 * 4 * NTHREADS, "solve scratch within the 16 KB work region");
 template <typename T>
 __device__ __noinline__ void blk_solve(int p, const T* Mb, int ldM, const T* rhs, T* y, T* out,
