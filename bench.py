@@ -481,6 +481,11 @@ def run_gpu(args):
     bstat = torch.empty((B,), device=dev, dtype=torch.int32)
     qp_backward(fwd, dl, out=[torch.empty_like(t) for t in gout], status=bstat)
     bstat = bstat.cpu().numpy()
+    uneven = None
+    if not args.no_extras and ws == 1:
+        uneven = {"untuned": uneven_run(dev, args.uneven_count, args.uneven_steps, False, flush, stream)}
+        if not args.no_tune:
+            uneven["tuned"] = uneven_run(dev, args.uneven_count, args.uneven_steps, True, flush, stream)
     served = None
     if not args.no_extras and ws == 1:
         served = serving_run(dev, [float(r) for r in str(args.serve_rate).split(",")],
@@ -516,6 +521,7 @@ def run_gpu(args):
         "batched_vs_plain": None if packed_ms is None else {
             "plain_fixed_size_ms_per_step": step_ms, "packed_persistent_ms_per_step": packed_ms,
             "note": "same 128 instances; packed = one persistent launch per direction over descriptors"},
+        "uneven": uneven,
         "served": served,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -548,6 +554,52 @@ def _time_fixed(Tin, gdev, steps, flush, stream):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     return statistics.mean(ms), f
+
+
+def uneven_run(dev, count, steps, tuned, flush, stream):
+    """The uneven workload: `count` QPs with n ~ U{8..256}, nineq ~ U{n/2..2n}, neq ~ U{0..n/4}
+    as one packed batch, forward (global-path and shared-memory-path instances in two
+    persistent kernels side by side) + backward (one persistent kernel), L2 flushed between
+    steps.  tuned: the autotuner's path choice and cost model."""
+    import torch
+    from paper_1703_00443_gb300 import inputs
+    from paper_1703_00443_gb300.packed import PackedBatch
+    sizes = inputs.uneven_sizes(count)
+    tuning = None
+    t0 = time.perf_counter()
+    if tuned:
+        from paper_1703_00443_gb300 import autotune
+        tuning = autotune.autotune(device=dev, save_to=None)
+    pb = PackedBatch(sizes, device=dev, tuning=tuning)
+    inst = [inputs.random_qp(nn, pp, mm, workload=inputs.WL_UNEVEN, index=i)
+            for i, (nn, pp, mm) in enumerate(sizes)]
+    gl = [inputs.upstream_grad(1, nn, workload=inputs.WL_UNEVEN, start=i)[0]
+          for i, (nn, pp, mm) in enumerate(sizes)]
+    P = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
+    G1 = pb.pack_vec([np.float32(x) for x in gl], "q")
+    tune_s = time.perf_counter() - t0
+    fo = pb.forward(*P)
+    go = pb.backward(P[0], P[2], P[4], G1)
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pb.forward(*P, out=fo)
+        pb.backward(P[0], P[2], P[4], G1, out=go)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    tm = statistics.mean(ms)
+    st = fo.status[:count].cpu().numpy()
+    return {"value": count / (tm / 1e3), "unit": UNIT, "ms_per_step": tm, "steps": steps,
+            "count": count, "global_path_instances": pb.n_global,
+            "tuned": bool(tuned), "tuning_s": tune_s if tuned else 0.0,
+            "workspace_gb": int(pb.sizes.ws_bytes) / 1e9,
+            "iters_mean": float(fo.iters[:count].float().mean()),
+            "converged": int((st == 0).sum()),
+            "sizes": "n~U{8..256}, nineq~U{n/2..2n}, neq~U{0..n/4}"}
 
 
 def run_workload(args):
@@ -592,43 +644,8 @@ def run_workload(args):
                      "value": B / (ms / 1e3), "ms_per_step": ms,
                      "iters_mean": float(f.iters.float().mean()), "converged": int((f.status == 0).sum())})
     elif args.workload == "uneven":
-        count = args.uneven_count
-        sizes = inputs.uneven_sizes(count)
-        tuning = None
-        if args.tuned:
-            from paper_1703_00443_gb300 import autotune
-            tuning = autotune.autotune(device=dev)
-        pb = PackedBatch(sizes, device=dev, tuning=tuning)
-        # per-instance data generated on the host (seeded, independent of the batch)
-        inst = [inputs.random_qp(nn, pp, mm, workload=inputs.WL_UNEVEN, index=i)
-                for i, (nn, pp, mm) in enumerate(sizes)]
-        gl = [inputs.upstream_grad(1, nn, workload=inputs.WL_UNEVEN, start=i)[0]
-              for i, (nn, pp, mm) in enumerate(sizes)]
-        P = pb.pack([tuple(np.float32(x) for x in t) for t in inst])
-        G1 = pb.pack_vec([np.float32(x) for x in gl], "q")
-        fo = pb.forward(*P)
-        go = pb.backward(P[0], P[2], P[4], G1)
-        torch.cuda.synchronize()
-        ms = []
-        for k in range(args.uneven_steps):
-            flush.fill_(float(k))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pb.forward(*P, out=fo)
-            pb.backward(P[0], P[2], P[4], G1, out=go)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        t = statistics.mean(ms)
-        st = fo.status[:count].cpu().numpy()
-        line.update({"metric": "uneven batch fwd+bwd solves/sec (one persistent launch each way)",
-                     "value": count / (t / 1e3), "ms_per_step": t, "count": count,
-                     "global_path_instances": pb.n_global,
-                     "tuned": bool(args.tuned),
-                     "workspace_gb": int(pb.sizes.ws_bytes) / 1e9,
-                     "iters_mean": float(fo.iters[:count].float().mean()),
-                     "converged": int((st == 0).sum()),
-                     "sizes": "n~U{8..256}, nineq~U{n/2..2n}, neq~U{0..n/4}"})
+        line.update({"metric": "uneven batch fwd+bwd solves/sec (two persistent kernels forward, one backward)"})
+        line.update(uneven_run(dev, args.uneven_count, args.uneven_steps, args.tuned, flush, stream))
     print(json.dumps(line), flush=True)
 
 
@@ -651,6 +668,8 @@ def main():
                     help="sweep points n:batch, comma-separated (default: the full grid)")
     ap.add_argument("--uneven-steps", type=int, default=3)
     ap.add_argument("--tuned", action="store_true", help="autotune the packed schedule first")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="main line: report the uneven workload untuned only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -11,7 +11,9 @@
  *
  * Layout: every matrix and vector argument is a DEVICE pointer to dense, row-major,
  * batch-major data (instance b of Q starts at Q + b·n·n, of G at G + b·nineq·n, ...),
- * of the element type chosen by `dtype`.  Q must be symmetric positive definite.
+ * of the element type chosen by `dtype`.  Q must be symmetric positive semidefinite, and the
+ * KKT system nonsingular at the solution (Q positive definite on the null space of the
+ * active constraints and of A, A of full row rank).
  * Pointers must be aligned to the element size.  All calls are asynchronous on `stream`
  * (a cudaStream_t, NULL = legacy default stream) and never synchronise the host.
  *
@@ -72,6 +74,12 @@ extern "C" {
  * proof of Theorem 1 no longer gives a unique derivative (the gradient returned there is
  * one element of a set). */
 #define QP_FLAG_NEAR_DEGENERATE 0x100
+/* Flag bit of backward status words: Q was only positive semidefinite (a pivot of Q in the
+ * setup fell below 1e-5, FP64 1e-12, of max_i Q_ii), so the factorisations used Q + δI with
+ * δ = 1e-4 (FP64 1e-8) × max(max_i Q_ii, squared row norms of G and A); the KKT residual that
+ * drives the iteration and the backward refinement use Q itself, so the results are those of
+ * the QP with Q. */
+#define QP_FLAG_REGULARIZED_Q 0x200
 
 typedef struct qp_options {
   double  tol;       /* stop when ‖r_z‖∞ ≤ tol·(1+‖q‖∞), ‖Gz+s−h‖∞ ≤ tol·(1+‖h‖∞),
@@ -206,8 +214,10 @@ typedef struct qp_packed_sizes {
 } qp_packed_sizes;
 
 /* Host-side planning: dims is a HOST array of B triples (n, nineq, neq).  Fills the HOST
- * arrays desc[B] (in execution order: largest estimated cost first) and *sizes.  The caller
- * copies desc to device memory unchanged and passes it, with sizes, to the packed calls. */
+ * arrays desc[B] (in execution order: the sizes->n_global global-path instances first, then
+ * the shared-memory-path ones, each part largest estimated cost first) and *sizes.  The
+ * caller copies desc to device memory unchanged and passes it, with sizes, to the packed
+ * calls. */
 int qp_packed_plan(const qp_options* opt, int dtype, int B, const int32_t* dims,
                    qp_instance_desc* desc, qp_packed_sizes* sizes);
 
@@ -220,7 +230,12 @@ int qp_packed_plan_ex(const qp_options* opt, int dtype, int B, const int32_t* di
                       qp_packed_sizes* sizes);
 
 /* Forward pass of a packed batch (device pointers as in qp_forward, packed as above;
- * status/iters/resid indexed by instance id; workspace of sizes->ws_bytes bytes). */
+ * status/iters/resid indexed by instance id; workspace of sizes->ws_bytes bytes).  When a
+ * batch holds both kinds, the global-path and shared-memory-path instances run as two
+ * persistent kernels side by side: the global-path one first, on `stream`, the other on a
+ * library-owned side stream forked from `stream` and joined back to it by events (created on
+ * a device's first such call: make that call before any stream capture).  Its blocks take
+ * SMs as the global-path blocks finish their queue. */
 int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
                       const qp_packed_sizes* sizes, const void* Q, const void* q,
                       const void* G, const void* h, const void* A, const void* b, void* z,

@@ -8,5 +8,5 @@ fails loudly if it cannot.
 from .qp import (QPError, ForwardResult, alloc_workspace, default_options, qp_backward,  # noqa: F401
                  qp_forward, supported, workspace_bytes, STATUS_CONVERGED, STATUS_MAX_ITER,
                  STATUS_NOT_PD, STATUS_NUMERICAL, STATUS_NO_FORWARD, STATUS_INFEASIBLE,
-                 STATUS_TIMEOUT, FLAG_NEAR_DEGENERATE)
+                 STATUS_TIMEOUT, FLAG_NEAR_DEGENERATE, FLAG_REGULARIZED_Q)
 from .autograd import QPFunction, qp_layer  # noqa: F401

@@ -3,6 +3,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "qp_gb300.h"
@@ -65,14 +66,14 @@ size_t fwd_smem(int dtype, int n, int nz, int nineq, int neq, bool large) {
   return L.total;
 }
 
-size_t bwd_smem(int dtype, int n, int nz, int nineq, int neq) {
+size_t bwd_smem(int dtype, int n, int nz, int nineq, int neq, bool staged = false) {
   if (dtype == QP_F32) {
     qpk::BwdSmem<float> L;
-    L.init(n, nz, nineq, neq);
+    L.init(n, nz, nineq, neq, staged);
     return L.total;
   }
   qpk::BwdSmem<double> L;
-  L.init(n, nz, nineq, neq);
+  L.init(n, nz, nineq, neq, staged);
   return L.total;
 }
 
@@ -80,9 +81,9 @@ size_t bwd_smem(int dtype, int n, int nz, int nineq, int neq) {
 // its factors fit in shared memory, else the global-memory kernel.  A pure function of the
 // sizes and the device's shared-memory limit, so forward and backward always agree.
 struct Plan {
-  bool ok = false, large = false;
+  bool ok = false, large = false, bstaged = false;
   int sw = 0, ch = 0, nz = 0;
-  size_t fsmem = 0, bsmem = 0, ws = 0;
+  size_t fsmem = 0, bsmem = 0, bsmem_staged = 0, ws = 0;
 };
 
 // force: 0 automatic, 1 global-memory path, 2 shared-memory path (ok = false if impossible).
@@ -105,6 +106,14 @@ Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
   }
   pl.fsmem = fwd_smem(dtype, n, pl.nz, nineq, neq, pl.large);
   pl.bsmem = bwd_smem(dtype, n, pl.nz, nineq, neq);
+  // The fixed-size backward kernel stages S/RE and X in shared memory when they fit there.
+  if (!pl.large) {
+    const size_t st = bwd_smem(dtype, n, pl.nz, nineq, neq, true);
+    if (st <= lim) {
+      pl.bsmem_staged = st;
+      pl.bstaged = true;
+    }
+  }
   qpk::WsLayout W;
   W.init(n, pl.nz, nineq, neq, dtype == QP_F32 ? 4 : 8, pl.large);
   pl.ws = W.inst;
@@ -115,6 +124,35 @@ Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
 }  // namespace
 
 static_assert(sizeof(qp_instance_desc) == sizeof(qpk::PackedDesc), "descriptor layout");
+
+// A non-blocking side stream and a fork/join event pair per device, created on first use (a
+// host-side resource, not device memory) and kept for the life of the process.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  std::mutex mu;
+};
+
+SideStream* side_stream() {
+  static std::mutex mu;
+  static SideStream slots[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  SideStream& x = slots[dev];
+  if (!x.s) {
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  return &x;
+}
 
 int num_sms() {
   int dev = 0, v = 0;
@@ -244,11 +282,12 @@ int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, i
   const Plan pl = make_plan(dtype, n, nineq, neq, o.path);
   if (workspace_bytes < (size_t)B * pl.ws) return QP_ENOSPACE;
   if (!pl.ok) return QP_EUNSUPPORTED;
-  const size_t smem = pl.bsmem;
+  const size_t smem = pl.bstaged ? pl.bsmem_staged : pl.bsmem;
+  const int staged = pl.bstaged ? 1 : 0;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (dtype == QP_F32) {
-    qpk::BwdParams<float> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0,
+    qpk::BwdParams<float> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0, staged,
                             (const float*)Q, (const float*)G, (const float*)A,
                             (const float*)dl_dz, (float*)dQ, (float*)dq, (float*)dG, (float*)dh,
                             (float*)dA, (float*)db, (const unsigned char*)workspace,
@@ -256,7 +295,7 @@ int qp_backward_ext(const qp_options* opt, int dtype, int B, int n, int nineq, i
                             status};
     e = qpk::launch_bwd_f32(P, smem, st);
   } else {
-    qpk::BwdParams<double> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0,
+    qpk::BwdParams<double> P{B, n, nineq, neq, pl.nz, pl.large ? 1 : 0, staged,
                              (const double*)Q, (const double*)G,
                              (const double*)A, (const double*)dl_dz, (double*)dQ, (double*)dq,
                              (double*)dG, (double*)dh, (double*)dA, (double*)db,
@@ -319,10 +358,14 @@ int qp_packed_plan_ex(const qp_options* opt, int dtype, int B, const int32_t* di
     for (int k = 0; k < 3; ++k)
       if (sws[k] >= sw_need && qpk::fwd_variant_exists(esz, sws[k], c)) { sw = sws[k]; ch = c; break; }
   if (!sw) return QP_EUNSUPPORTED;
-  // Execution order: largest estimated cost first (longest-processing-time schedule).
-  std::stable_sort(order.begin(), order.end(),
-                   [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+  // Execution order: global-path instances first, then shared-memory-path ones (the two run
+  // as separate kernels), each part largest estimated cost first (longest-processing-time).
   std::vector<qp_instance_desc> tmp(desc, desc + B);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+                     const int gx = tmp[x.second].flags & 1, gy = tmp[y.second].flags & 1;
+                     return gx != gy ? gx > gy : x.first > y.first;
+                   });
   for (int k = 0; k < B; ++k) desc[k] = tmp[order[k].second];
   S.nQ = oQ; S.nq = oq; S.nG = oG; S.nh = oh; S.nA = oA; S.nb = ob;
   S.nz = oq; S.nlam = oh; S.nnu = ob;
@@ -350,25 +393,53 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
   if (o.max_iter < 0 || o.time_limit_us < 0) return QP_EINVAL;
   const unsigned long long tl_ns = 1000ull * (unsigned long long)o.time_limit_us;
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemsetAsync(workspace, 0, 8, st) != cudaSuccess) return QP_ECUDA;
-  const int grid = std::min(B, num_sms());
-  cudaError_t e;
-  if (dtype == QP_F32) {
-    qpk::PackedFwdParams<float> P{B, (const qpk::PackedDesc*)desc, (int*)workspace,
-                                  (const float*)Q, (const float*)q, (const float*)G, (const float*)h,
-                                  (const float*)A, (const float*)b, (float*)z, (float*)lam, (float*)nu,
-                                  status, iters, resid, (unsigned char*)workspace,
-                                  o.tol, o.mu_tol, o.max_iter, tl_ns};
-    e = qpk::launch_fwd_packed_f32(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
-                                      sizes->n_global > 0, st);
-  } else {
-    qpk::PackedFwdParams<double> P{B, (const qpk::PackedDesc*)desc, (int*)workspace,
+  // Work-queue counters: bytes 0..3 the shared-memory-path kernel's, 4..7 the backward's,
+  // 8..11 the kernel of the global-path instances.
+  if (cudaMemsetAsync(workspace, 0, 16, st) != cudaSuccess) return QP_ECUDA;
+  const int nsm = num_sms(), ng = std::min(std::max(sizes->n_global, 0), B), ns = B - ng;
+  auto launch = [&](int mode, int off, int cnt, int grid, int ctr_byte, cudaStream_t s) {
+    if (dtype == QP_F32) {
+      qpk::PackedFwdParams<float> P{cnt, (const qpk::PackedDesc*)desc + off,
+                                    (int*)((char*)workspace + ctr_byte),
+                                    (const float*)Q, (const float*)q, (const float*)G,
+                                    (const float*)h, (const float*)A, (const float*)b, (float*)z,
+                                    (float*)lam, (float*)nu, status, iters, resid,
+                                    (unsigned char*)workspace, o.tol, o.mu_tol, o.max_iter, tl_ns};
+      return qpk::launch_fwd_packed_f32(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
+                                        mode, s);
+    }
+    qpk::PackedFwdParams<double> P{cnt, (const qpk::PackedDesc*)desc + off,
+                                   (int*)((char*)workspace + ctr_byte),
                                    (const double*)Q, (const double*)q, (const double*)G,
                                    (const double*)h, (const double*)A, (const double*)b,
                                    (double*)z, (double*)lam, (double*)nu, status, iters, resid,
                                    (unsigned char*)workspace, o.tol, o.mu_tol, o.max_iter, tl_ns};
-    e = qpk::launch_fwd_packed_f64(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
-                                      sizes->n_global > 0, st);
+    return qpk::launch_fwd_packed_f64(P, sizes->sw, sizes->ch, (size_t)sizes->fwd_smem, grid,
+                                      mode, s);
+  };
+  cudaError_t e;
+  if (ns == 0) {
+    e = launch(qpk::PK_BOTH, 0, ng, std::min(ng, nsm), 8, st);
+  } else if (ng == 0) {
+    e = launch(qpk::PK_SMEM, 0, ns, std::min(ns, nsm), 0, st);
+  } else {
+    // Both kinds: the global-path instances (first in the descriptor array) in the combined
+    // kernel on `stream`, launched first so that its blocks take the SMs first; the
+    // shared-memory-path instances in the shared-memory-only kernel on a side stream forked
+    // from `stream` and joined back to it.  Each block of either kernel holds its SM until its
+    // queue runs dry, so as global-path blocks finish, shared-memory-path blocks take their
+    // SMs: the hardware block scheduler balances the two queues without a fixed split.
+    SideStream* ss = side_stream();
+    if (!ss) return QP_ECUDA;
+    std::lock_guard<std::mutex> lk(ss->mu);
+    if (cudaEventRecord(ss->fork, st) != cudaSuccess) return QP_ECUDA;
+    e = launch(qpk::PK_BOTH, 0, ng, std::min(ng, nsm), 8, st);
+    if (e != cudaSuccess) return QP_ECUDA;
+    if (cudaStreamWaitEvent(ss->s, ss->fork, 0) != cudaSuccess) return QP_ECUDA;
+    e = launch(qpk::PK_SMEM, ng, ns, std::min(ns, nsm), 0, ss->s);
+    if (cudaEventRecord(ss->join, ss->s) != cudaSuccess ||
+        cudaStreamWaitEvent(st, ss->join, 0) != cudaSuccess)
+      return QP_ECUDA;
   }
   return e == cudaSuccess ? QP_OK : QP_ECUDA;
 }

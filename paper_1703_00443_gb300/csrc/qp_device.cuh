@@ -64,6 +64,9 @@ enum : int { ST_CONV = 0, ST_MAXIT = 1, ST_NOTPD = 2, ST_NUM = 3, ST_NOFWD = 4, 
 // Flag bit of the status word kept in the workspace (reported by the backward pass): a nearly
 // degenerate complementarity pair at the returned iterate.
 constexpr int FLAG_NEARDEG = 0x100;
+// Flag bit: Q was only positive semidefinite and the factorisations used Q + δI (the
+// residual and the backward refinement use Q itself).
+constexpr int FLAG_REGQ = 0x200;
 // Magic word of the workspace stamp the forward pass leaves for the backward pass.
 constexpr int32_t STAMP_MAGIC = 0x51504657;
 
@@ -195,10 +198,16 @@ struct FwdSmem {
 // Dynamic shared memory of the backward kernel (vectors only).
 template <typename T>
 struct BwdSmem {
-  size_t odbl, osplit, ovec, ored, oscr, total;
-  __host__ __device__ void init(int n, int nz, int p, int m) {
+  size_t odbl, osplit, ovec, ored, oscr, oSR, oX, total;
+  // staged: S/RE and X = L⁻¹ are copied from the workspace into shared memory first.
+  __host__ __device__ void init(int n, int nz, int p, int m, bool staged = false) {
     const size_t m1 = (size_t)nz + m, es = sizeof(T);
     size_t o = 0;
+    oSR = oX = 0;
+    if (staged) {
+      oSR = o; o = align_up(o + (m1 + p) * m1 * es, 16);
+      oX = o;  o = align_up(o + (size_t)p * p * es, 16);
+    }
     odbl = o;   o = align_up(o + 8 * (3 * ((size_t)n + p + m) + 2 * (size_t)p), 16);
     osplit = o; o = align_up(o + 8 * ((size_t)n + p + m), 16);
     ovec = o;   o = align_up(o + es * (3 * m1 + 4 * (size_t)(p + 3) / 4 * 4), 16);
@@ -239,7 +248,7 @@ struct FwdInst {
 
 template <typename T>
 struct BwdInst {
-  int n, p, m, nz, large;
+  int n, p, m, nz, large, staged;
   const T *Q, *G, *A, *dl_dz;
   T *dQ, *dq, *dG, *dh, *dA, *db;
   const unsigned char* ws;
@@ -286,6 +295,7 @@ template <typename T>
 struct BwdParams {
   int B, n, p, m, nz;
   int large;
+  int staged;   // S/RE and X staged in shared memory (BwdSmem with staged = true)
   const T *Q, *G, *A, *dl_dz;
   T *dQ, *dq, *dG, *dh, *dA, *db;
   const unsigned char* ws;
@@ -833,14 +843,14 @@ __device__ __forceinline__ T sel4(T a0, T a1, T a2, T a3, int k) {
 }
 
 // Element (i, j) of the symmetric matrix [[Q̃, Aᵀ, Gᵀ], [A, 0, 0], [G, 0, 0]] whose first
-// m1 = nz + neq pivots are swept (rows ordered z, dummies, ν, λ; Q̃ = Q ⊕ I on the dummy
-// variables).  Zero outside N×N.
+// m1 = nz + neq pivots are swept (rows ordered z, dummies, ν, λ; Q̃ = (Q + δI) ⊕ I on the
+// dummy variables, δ = 0 unless Q is only positive semidefinite).  Zero outside N×N.
 template <typename T>
 __device__ __forceinline__ T k3_elem(int n, int nz, int m1, int N, const T* Q, const T* A,
-                                     const T* G, int i, int j) {
+                                     const T* G, int i, int j, T delta) {
   if (i >= N || j >= N) return T(0);
   if (i < j) { const int t = i; i = j; j = t; }
-  if (i < n) return Q[(size_t)i * n + j];
+  if (i < n) return (i == j) ? Q[(size_t)i * n + j] + delta : Q[(size_t)i * n + j];
   if (i < nz) return (i == j) ? T(1) : T(0);
   if (j >= n) return T(0);
   if (i < m1) return A[(size_t)(i - nz) * n + j];
@@ -914,7 +924,8 @@ __device__ __forceinline__ void st_panel(T* buf, int ld, int B, const T (&v)[16]
 template <typename T, int SW>
 __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restrict__ Q,
                                          const T* __restrict__ A, const T* __restrict__ G,
-                                         T* SR, int ldS, T* Mb, int ldM, T* dM, T* cb) {
+                                         T* SR, int ldS, T* Mb, int ldM, T* dM, T* cb,
+                                         T delta, T zthr) {
   const int tid = threadIdx.x;
   const int nz = padded_nz(n, m), m1 = nz + m, N = m1 + p;
   const int NT = (N + 3) >> 2, ntiles = NT * (NT + 1) / 2, KB = m1 >> 2;
@@ -936,7 +947,7 @@ __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restric
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         a[s][r * 4 + c] =
-            (I >= 0) ? k3_elem(n, nz, m1, N, Q, A, G, 4 * I + r, 4 * J + c) : T(0);
+            (I >= 0) ? k3_elem(n, nz, m1, N, Q, A, G, 4 * I + r, 4 * J + c, delta) : T(0);
   }
   for (int K = 0; K < KB; ++K) {
     T* Cb = cb + (K & 1) * pstride;
@@ -953,8 +964,10 @@ __device__ __noinline__ bool sweep_setup(int n, int p, int m, const T* __restric
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const T d = w[k * 4 + k];
-          const bool pos = (4 * K + k) < nz;
-          good = good && isfinite(d) && (pos ? d > T(0) : d < T(0));
+          const int kk = 4 * K + k;
+          // z pivots must clear zthr (a singular Q shows as a pivot at rounding level), dummy
+          // pivots 0, ν pivots must be negative (A of full row rank)
+          good = good && isfinite(d) && (kk < n ? d > zthr : (kk < nz ? d > T(0) : d < T(0)));
           const T dinv = T(1) / d;
 #pragma unroll
           for (int q = 0; q < 4; ++q) Rb[k * 4 + q] = (q == k) ? dinv : w[k * 4 + q] * dinv;
@@ -1308,6 +1321,26 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr, size_t bytes) {
     asm volatile("prefetch.global.L2 [%0];" :: "l"(c + o));
 }
 
+// Asynchronous 16-byte copy global → shared (cp.async), and the wait for all of a thread's.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Copies `bytes` bytes from global src to shared dst (both 16-byte aligned) with the whole
+// block: 16-byte asynchronous copies, the tail by bytes; ends with a barrier.
+__device__ __forceinline__ void stage_to_smem(unsigned char* dst, const unsigned char* src,
+                                              size_t bytes) {
+  const size_t n16 = bytes / 16;
+  for (size_t i = threadIdx.x; i < n16; i += NTHREADS) cp_async16(dst + 16 * i, src + 16 * i);
+  for (size_t i = 16 * n16 + threadIdx.x; i < bytes; i += NTHREADS) dst[i] = src[i];
+  cp_async_wait_all();
+  __syncthreads();
+}
+
 // Nanoseconds of the GPU's global timer.
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -1416,8 +1449,38 @@ __device__ __forceinline__ void fwd_body(const FwdInst<T>& P, const FwdSmem<T>& 
     return v[0] > 0.0 && v[0] > 1e3 * (1.0 + v[2]) * v[1];
   };
 
-  bool ok = setup(Qb, Ab, Gb);
+  // Setup factorisations.  Q may be only positive semidefinite (§3, Eq. 2): a z pivot at
+  // rounding level, below zthr = 1e-5 (FP64: 1e-12) of Q's largest diagonal entry, shows a
+  // singular Q, and the setup is repeated with Q + δI, δ = 1e-4 (FP64: 1e-8) of the largest
+  // of max_i Q_ii and the squared row norms of G and A.  The Newton systems then carry the
+  // regularisation, but the residual they are driven by is the exact one with Q, so the
+  // iteration is an inexact Newton method whose fixed point is the exact KKT point; the
+  // backward refinement likewise uses Q.
+  T delta = T(0);
+  float qmx;
+  {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)Qb[(size_t)i * n + i]));
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
+    qmx = v[0];
+  }
+  bool ok = setup(Qb, Ab, Gb, T(0), (T)((sizeof(T) == 4 ? 1e-5f : 1e-12f) * qmx));
   __syncthreads();
+  if (!ok) {
+    float v[4] = {qmx, 0.f, 0.f, 0.f};
+    for (int i = tid; i < p + m; i += NTHREADS) {
+      const T* row = i < p ? Gb + (size_t)i * n : Ab + (size_t)(i - p) * n;
+      float sq = 0.f;
+      for (int j = 0; j < n; ++j) sq = fmaf((float)row[j], (float)row[j], sq);
+      v[1] = fmaxf(v[1], sq);
+    }
+    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
+    const float scale = fmaxf(fmaxf(v[0], v[1]), 1e-30f);
+    delta = (T)((sizeof(T) == 4 ? 1e-4f : 1e-8f) * scale);
+    if (isfinite(scale)) ok = setup(Qb, Ab, Gb, delta, T(0));
+    __syncthreads();
+    if (ok) flags |= FLAG_REGQ;
+  }
   if (!ok) status = ST_NOTPD;
 
   // Stopping thresholds tol·(1 + ‖q‖∞), tol·(1 + ‖h‖∞), tol·(1 + ‖b‖∞) and mu_tol.
@@ -1775,8 +1838,8 @@ __device__ __forceinline__ void fwd_smem_path(const FwdInst<T>& I, unsigned char
   const int n = I.n, p = I.p, m = I.m;
   const int tcap = (int)(L.cbytes / sizeof(T));
   fwd_body<T>(I, L, sm, SR, Mb, L.ldM, dM, false,
-      [&](const T* Qb, const T* Ab, const T* Gb) {
-        return sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb);
+      [&](const T* Qb, const T* Ab, const T* Gb, T delta, T zthr) {
+        return sweep_setup<T, SW>(n, p, m, Qb, Ab, Gb, SR, L.ldS, Mb, L.ldM, dM, cb, delta, zthr);
       },
       [&](const T* dsh) { return chol_blk<T, CH, true>(p, Mb, L.ldM, dM, dsh, cb); },
       [&](const T* rhs, T* y, T* out, T* scr) { chol_solve(p, Mb, L.ldM, rhs, y, out, scr); });
@@ -1798,8 +1861,9 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
   T* cb = reinterpret_cast<T*>(sm + L.ocb);
   const int tcap = (int)(L.cbytes / sizeof(T));
   fwd_body<T>(I, L, sm, SR, Mb, p > 0 ? p : 1, dM, true,
-      [&](const T* Qb, const T* Ab, const T* Gb) {
-        return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, L.span_smem != 0, cb);
+      [&](const T* Qb, const T* Ab, const T* Gb, T delta, T zthr) {
+        return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, L.span_smem != 0, cb,
+                               delta, zthr);
       },
       [&](const T* dsh) {
         // Small Schur complements: the register-tile routine (M read from and X written to
@@ -1832,12 +1896,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_large_kernel(const FwdPara
   fwd_global_path<T>(fixed_inst(P, blockIdx.x), sm);
 }
 
-// Packed batch of uneven sizes in one persistent launch: blocks take instances from an atomic
-// counter in the order of the descriptor array (largest estimated cost first), and each
-// instance runs the path its own size selects, so its result does not depend on the mix.
-// WITH_GLOBAL = false compiles the shared-memory path alone (its registers then allocated as
-// in the fixed-size kernel); the host uses it for batches without global-path instances.
-template <typename T, int SW, int CH, bool WITH_GLOBAL>
+// Packed batch of uneven sizes, persistent: blocks take instances from an atomic counter in
+// the order of the descriptor array (largest estimated cost first), and each instance runs
+// the path its own size selects, so its result does not depend on the mix.  MODE selects the
+// code compiled in: PK_SMEM the shared-memory path alone (register-allocated on its own, as
+// the fixed-size kernel is), PK_BOTH both paths.  The host runs a batch's global-path
+// instances in a PK_BOTH kernel and its shared-memory-path instances in a PK_SMEM kernel
+// beside it, each over its own descriptor range.
+enum : int { PK_SMEM = 0, PK_BOTH = 1 };
+template <typename T, int SW, int CH, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const PackedFwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int s_idx;
@@ -1864,17 +1931,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const Packed
     I.ws = P.ws + d.ows;
     I.tol = P.tol; I.mu_tol = P.mu_tol; I.max_iter = P.max_iter;
     I.time_limit_ns = P.time_limit_ns;
-    if (d.flags & 1) {
-      if constexpr (WITH_GLOBAL) {
-        fwd_global_path<T>(I, sm);
-      } else if (threadIdx.x == 0) {
-        // Not reached (the host picks this kernel only when no instance needs the global
-        // path); should it happen, the instance is marked failed rather than run here.
+    const bool glob = (d.flags & 1) != 0;
+    if (glob && MODE == PK_SMEM) {
+      // Not reached (the host gives each kernel only instances of its own path); should it
+      // happen, the instance is marked failed rather than run on the wrong path.
+      if (threadIdx.x == 0) {
         WsLayout W;
-        W.init(I.n, I.nz, I.p, I.m, (int)sizeof(T), true);
+        W.init(I.n, I.nz, I.p, I.m, (int)sizeof(T), glob);
         reinterpret_cast<int32_t*>(I.ws + W.oSt)[0] = ST_NUM;
         if (I.status) *I.status = ST_NUM;
       }
+    } else if constexpr (MODE == PK_BOTH) {
+      if (glob) fwd_global_path<T>(I, sm);
+      else fwd_smem_path<T, SW, CH>(I, sm);
     } else {
       fwd_smem_path<T, SW, CH>(I, sm);
     }
@@ -1889,7 +1958,7 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   const int tid = threadIdx.x;
   const int n = P.n, p = P.p, m = P.m, nz = P.nz, m1 = nz + m;
   BwdSmem<T> L;
-  L.init(n, nz, p, m);
+  L.init(n, nz, p, m, P.staged != 0);
   double* dv = reinterpret_cast<double*>(sm + L.odbl);
   double *z = dv, *s = z + n, *lam = s + p, *nu = lam + p;
   double *dz = nu + m, *dlt = dz + n, *dnu = dlt + p;
@@ -1908,6 +1977,7 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   const unsigned char* wsb = P.ws;
   const T* SR = reinterpret_cast<const T*>(wsb + W.oSR);
   const T* X = reinterpret_cast<const T*>(wsb + W.oX);
+  const bool stage = P.staged != 0;
   const double* wIt = reinterpret_cast<const double*>(wsb + W.oIt);
   const T* Qb = P.Q;
   const T* Gb = p ? P.G : nullptr;
@@ -1935,8 +2005,16 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[i] = qn;
     return;
   }
-  // Everything read below: S/RE and the factor (workspace), Q, G, A (refinement residual).
-  prefetch_l2(X, (size_t)p * p * sizeof(T));
+  // S/RE and X into shared memory when the host planned room for them (they are read by two
+  // S/RE products, two REᵀ products and four products with X).
+  if (stage) {
+    stage_to_smem(sm + L.oSR, wsb + W.oSR, (size_t)(m1 + p) * m1 * sizeof(T));
+    stage_to_smem(sm + L.oX, wsb + W.oX, (size_t)p * p * sizeof(T));
+    SR = reinterpret_cast<const T*>(sm + L.oSR);
+    X = reinterpret_cast<const T*>(sm + L.oX);
+  }
+  // Everything else read below from global memory: Q, G, A (refinement residual).
+  if (!stage) prefetch_l2(X, (size_t)p * p * sizeof(T));
   prefetch_l2(Qb, (size_t)n * n * sizeof(T));
   prefetch_l2(Gb, (size_t)p * n * sizeof(T));
   prefetch_l2(Ab, (size_t)m * n * sizeof(T));
@@ -2082,7 +2160,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_kernel(const BwdParams<T> 
   extern __shared__ __align__(16) unsigned char sm[];
   const int bi = blockIdx.x, n = P.n, p = P.p, m = P.m;
   BwdInst<T> I;
-  I.n = n; I.p = p; I.m = m; I.nz = P.nz; I.large = P.large;
+  I.n = n; I.p = p; I.m = m; I.nz = P.nz; I.large = P.large; I.staged = P.staged;
   I.Q = P.Q + (size_t)bi * n * n;
   I.G = p ? P.G + (size_t)bi * p * n : nullptr;
   I.A = m ? P.A + (size_t)bi * m * n : nullptr;
@@ -2114,7 +2192,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_bwd_packed_kernel(const Packed
     if (k >= P.B) break;
     const PackedDesc d = P.desc[k];
     BwdInst<T> I;
-    I.n = d.n; I.p = d.nineq; I.m = d.neq; I.nz = d.nz; I.large = d.flags & 1;
+    I.n = d.n; I.p = d.nineq; I.m = d.neq; I.nz = d.nz; I.large = d.flags & 1; I.staged = 0;
     I.Q = P.Q + d.oQ;
     I.G = d.nineq ? P.G + d.oG : nullptr;
     I.A = d.neq ? P.A + d.oA : nullptr;

@@ -29,10 +29,10 @@ cudaError_t launch_fwd_large_f32(const FwdParams<float>& P, size_t smem, cudaStr
 }
 
 template <int SW, int CH>
-static cudaError_t gop(const PackedFwdParams<float>& P, size_t smem, int grid, bool with_global,
+static cudaError_t gop(const PackedFwdParams<float>& P, size_t smem, int grid, int mode,
                        cudaStream_t st) {
-  auto k = with_global ? qp_fwd_packed_kernel<float, SW, CH, true>
-                       : qp_fwd_packed_kernel<float, SW, CH, false>;
+  auto k = mode == PK_BOTH ? qp_fwd_packed_kernel<float, SW, CH, PK_BOTH>
+                           : qp_fwd_packed_kernel<float, SW, CH, PK_SMEM>;
   cudaError_t e = prepare_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, NTHREADS, smem, st>>>(P);
@@ -40,11 +40,11 @@ static cudaError_t gop(const PackedFwdParams<float>& P, size_t smem, int grid, b
 }
 
 cudaError_t launch_fwd_packed_f32(const PackedFwdParams<float>& P, int SW, int CH, size_t smem,
-                                  int grid, bool with_global, cudaStream_t st) {
-  if (SW == 1 && CH == 1) return gop<1, 1>(P, smem, grid, with_global, st);
-  if (SW == 2 && CH == 1) return gop<2, 1>(P, smem, grid, with_global, st);
-  if (SW == 4 && CH == 1) return gop<4, 1>(P, smem, grid, with_global, st);
-  if (SW == 4 && CH == 2) return gop<4, 2>(P, smem, grid, with_global, st);
+                                  int grid, int mode, cudaStream_t st) {
+  if (SW == 1 && CH == 1) return gop<1, 1>(P, smem, grid, mode, st);
+  if (SW == 2 && CH == 1) return gop<2, 1>(P, smem, grid, mode, st);
+  if (SW == 4 && CH == 1) return gop<4, 1>(P, smem, grid, mode, st);
+  if (SW == 4 && CH == 2) return gop<4, 2>(P, smem, grid, mode, st);
   return cudaErrorInvalidValue;
 }
 

@@ -27,10 +27,10 @@ cudaError_t launch_fwd_large_f64(const FwdParams<double>& P, size_t smem, cudaSt
 }
 
 template <int SW, int CH>
-static cudaError_t gop(const PackedFwdParams<double>& P, size_t smem, int grid, bool with_global,
+static cudaError_t gop(const PackedFwdParams<double>& P, size_t smem, int grid, int mode,
                        cudaStream_t st) {
-  auto k = with_global ? qp_fwd_packed_kernel<double, SW, CH, true>
-                       : qp_fwd_packed_kernel<double, SW, CH, false>;
+  auto k = mode == PK_BOTH ? qp_fwd_packed_kernel<double, SW, CH, PK_BOTH>
+                           : qp_fwd_packed_kernel<double, SW, CH, PK_SMEM>;
   cudaError_t e = prepare_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, NTHREADS, smem, st>>>(P);
@@ -38,9 +38,9 @@ static cudaError_t gop(const PackedFwdParams<double>& P, size_t smem, int grid, 
 }
 
 cudaError_t launch_fwd_packed_f64(const PackedFwdParams<double>& P, int SW, int CH, size_t smem,
-                                  int grid, bool with_global, cudaStream_t st) {
-  if (SW == 1 && CH == 1) return gop<1, 1>(P, smem, grid, with_global, st);
-  if (SW == 2 && CH == 1) return gop<2, 1>(P, smem, grid, with_global, st);
+                                  int grid, int mode, cudaStream_t st) {
+  if (SW == 1 && CH == 1) return gop<1, 1>(P, smem, grid, mode, st);
+  if (SW == 2 && CH == 1) return gop<2, 1>(P, smem, grid, mode, st);
   return cudaErrorInvalidValue;
 }
 

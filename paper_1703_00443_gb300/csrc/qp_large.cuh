@@ -33,7 +33,8 @@ __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 template <typename T>
 __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* __restrict__ Q,
                                           const T* __restrict__ A, const T* __restrict__ G,
-                                          T* SR, T* Mb, T* dM, T* pan, bool pan_in_sm, T* sm) {
+                                          T* SR, T* Mb, T* dM, T* pan, bool pan_in_sm, T* sm,
+                                          T delta, T zthr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m1 = nz + m, N = m1 + p, ldS = m1, ldM = p > 0 ? p : 1;
   const bool mvec = (p & 3) == 0;   // rows of Mb 16-byte aligned
@@ -46,7 +47,7 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
 
   for (int e = tid; e < (m1 + p) * m1; e += NTHREADS) {
     const int i = e / m1, j = e - i * m1;
-    SR[e] = k3_elem(n, nz, m1, N, Q, A, G, i, j);
+    SR[e] = k3_elem(n, nz, m1, N, Q, A, G, i, j, delta);
   }
   for (int e = tid; e < p * p; e += NTHREADS) Mb[e] = T(0);
   for (int e = tid; e < p; e += NTHREADS) dM[e] = T(0);
@@ -63,7 +64,8 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
       bool good = true;
       for (int k = 0; k < LNB; ++k) {
         const T d = sB[k * LNB + k];
-        good = good && isfinite(d) && ((k0 + k) < nz ? d > T(0) : d < T(0));
+        const int kk = k0 + k;
+        good = good && isfinite(d) && (kk < n ? d > zthr : (kk < nz ? d > T(0) : d < T(0)));
         const T dinv = T(1) / d;
         if (lane < LNB) sR[k * LNB + lane] = (lane == k) ? dinv : sB[k * LNB + lane] * dinv;
         T upd[LNB * LNB / 32];

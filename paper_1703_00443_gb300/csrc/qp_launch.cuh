@@ -21,9 +21,9 @@ cudaError_t launch_fwd_f64(const FwdParams<double>& P, int SW, int CH, size_t sm
 cudaError_t launch_fwd_large_f32(const FwdParams<float>& P, size_t smem, cudaStream_t st);
 cudaError_t launch_fwd_large_f64(const FwdParams<double>& P, size_t smem, cudaStream_t st);
 cudaError_t launch_fwd_packed_f32(const PackedFwdParams<float>& P, int SW, int CH, size_t smem,
-                                  int grid, bool with_global, cudaStream_t st);
+                                  int grid, int mode, cudaStream_t st);
 cudaError_t launch_fwd_packed_f64(const PackedFwdParams<double>& P, int SW, int CH, size_t smem,
-                                  int grid, bool with_global, cudaStream_t st);
+                                  int grid, int mode, cudaStream_t st);
 cudaError_t launch_bwd_packed_f32(const PackedBwdParams<float>& P, size_t smem, int grid, cudaStream_t st);
 cudaError_t launch_bwd_packed_f64(const PackedBwdParams<double>& P, size_t smem, int grid, cudaStream_t st);
 cudaError_t launch_bwd_f32(const BwdParams<float>& P, size_t smem, cudaStream_t st);

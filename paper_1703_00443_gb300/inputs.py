@@ -31,6 +31,8 @@ WL_SWEEP = 1        # same recipe at the timing-sweep sizes
 WL_ONEHOT = 2       # structured one-hot QP (Q = 0.1 I, z >= 0, dense equalities)
 WL_UNEVEN = 3       # uneven batch: per-instance sizes drawn too
 WL_SERVE = 4        # serving stream
+WL_PSD = 5          # positive semidefinite Q (LPs with rank 0)
+WL_TV = 6           # total-variation denoising (§4.2) on synthetic signals
 
 
 @dataclasses.dataclass
@@ -115,6 +117,55 @@ def onehot_qp(n: int = 64, neq: int = 40, *, seed: int = 0, index: int = 0, dtyp
     Q, q, G, h, A = (_round(x, dtype) for x in (Q, q, G, h, A))
     b = _round(A @ u, dtype)
     return Q, q, G, h, A, b
+
+
+def psd_qp(n: int, nineq_extra: int, neq: int, rank: int, *, seed: int = 0, index: int = 0,
+           dtype=np.float32):
+    """A QP with positive semidefinite Q of the given rank (rank 0: a linear program):
+    Q = L Lᵀ with L ~ N(0,1)/√n (n × rank), q ~ N(0,1), the box −1 ≤ z ≤ 1 plus nineq_extra
+    rows G ~ N(0,1) with h = G z0 + s0 (z0 ~ U(−0.3, 0.3), s0 ~ U(0.2, 1)), A ~ N(0,1), b = A z0,
+    so the feasible set is bounded with z0 strictly inside it."""
+    r = _rng(seed, WL_PSD, index)
+    L = r.standard_normal((n, rank)) / math.sqrt(n)
+    Q = L @ L.T
+    Q = 0.5 * (Q + Q.T)
+    q = r.standard_normal(n)
+    Gr = r.standard_normal((nineq_extra, n))
+    z0 = r.uniform(-0.3, 0.3, n)
+    s0 = r.uniform(0.2, 1.0, nineq_extra)
+    A = r.standard_normal((neq, n))
+    Q, q, Gr, A, z0 = (_round(x, dtype) for x in (Q, q, Gr, A, z0))
+    G = np.vstack([np.eye(n), -np.eye(n), Gr])
+    h = np.concatenate([np.ones(2 * n), _round(Gr @ z0 + s0, dtype)])
+    b = _round(A @ z0, dtype)
+    return Q, q, G, h, A, b
+
+
+def tv_qp(y, w: float, D=None):
+    """Total-variation denoising (§4.2) as a QP in (z, t), FP64:
+    minimise ½‖y − z‖² + w·1ᵀt subject to Dz − t ≤ 0 and −Dz − t ≤ 0, with D the first
+    difference (n−1)×n unless another operator is given (the learned-D variant).
+    Q = diag(I, 0) is positive semidefinite."""
+    y = np.asarray(y, dtype=np.float64)
+    n = len(y)
+    D = np.diff(np.eye(n), axis=0) if D is None else np.asarray(D, dtype=np.float64)
+    k = D.shape[0]
+    Q = np.zeros((n + k, n + k))
+    Q[:n, :n] = np.eye(n)
+    q = np.concatenate([-y, w * np.ones(k)])
+    G = np.block([[D, -np.eye(k)], [-D, -np.eye(k)]])
+    h = np.zeros(2 * k)
+    return Q, q, G, h, np.zeros((0, n + k)), np.zeros(0)
+
+
+def tv_signal(n: int, *, seed: int = 0, index: int = 0, noise: float = 0.2) -> np.ndarray:
+    """Piecewise-constant signal (3 levels ~ U(−1, 1), random breakpoints) plus N(0, noise²)."""
+    r = _rng(seed, WL_TV, index)
+    cuts = np.sort(r.choice(np.arange(1, n), 2, replace=False))
+    levels = r.uniform(-1.0, 1.0, 3)
+    x = np.concatenate([np.full(cuts[0], levels[0]), np.full(cuts[1] - cuts[0], levels[1]),
+                        np.full(n - cuts[1], levels[2])])
+    return x + noise * r.standard_normal(n)
 
 
 def stack(instances) -> QPBatch:

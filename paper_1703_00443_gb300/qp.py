@@ -21,6 +21,7 @@ QP_F32, QP_F64 = 0, 1
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NOT_PD, STATUS_NUMERICAL = 0, 1, 2, 3
 STATUS_NO_FORWARD, STATUS_INFEASIBLE, STATUS_TIMEOUT = 4, 5, 6
 FLAG_NEAR_DEGENERATE = 0x100   # in backward status words (status & 0xff is the code)
+FLAG_REGULARIZED_Q = 0x200     # backward status word: Q was singular, Q + δI was factored
 
 
 class QPError(RuntimeError):

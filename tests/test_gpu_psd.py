@@ -1,0 +1,88 @@
+"""Positive semidefinite Q on the GPU (§3, Eq. 2 allows Q ⪰ 0): linear programs (Q = 0),
+rank-deficient Q and the TV-denoising QP of §4.2 (Q = diag(I, 0)), against the FP64 oracle.
+The kernels factor Q + δI when Q is singular and drive the iteration and the backward
+refinement with the exact residual of Q; the backward status carries the flag."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1703_00443_gb300 import (FLAG_REGULARIZED_Q, STATUS_CONVERGED, default_options,
+                                    inputs, qp_backward, qp_forward)
+from tests.helpers import grad_floor, oracle_many, rel_err, rel_err_inf
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+NAMES = ("dQ", "dq", "dG", "dh", "dA", "db")
+
+
+def _batch(insts):
+    return inputs.stack(insts)
+
+
+def _run_and_compare(batch, g, dtype, ztol, gtol, ltol, options=None):
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    T = [torch.from_numpy(np.ascontiguousarray(x)).to(DEV, tdt) for x in
+         (batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b)]
+    fwd = qp_forward(*T, options=options)
+    st = torch.full((batch.B,), -1, dtype=torch.int32, device=DEV)
+    grads = qp_backward(fwd, torch.from_numpy(np.ascontiguousarray(g)).to(DEV, tdt), status=st)
+    torch.cuda.synchronize()
+    assert (fwd.status.cpu().numpy() == STATUS_CONVERGED).all(), fwd.status
+    out = dict(z=fwd.z, lam=fwd.lam, nu=fwd.nu)
+    out.update(zip(NAMES, grads))
+    out = {k: v.double().cpu().numpy() for k, v in out.items()}
+    refs = oracle_many([batch.instance(i) + (np.float64(g[i]),) for i in range(batch.B)])
+    for i, (sol, gr) in enumerate(refs):
+        assert sol["status"] == 0
+        for k, ref, tol, gname in [("z", sol["z"], ztol, None), ("lam", sol["lam"], ltol, None),
+                                   ("nu", sol["nu"], ltol, None)] + [(k, gr[k], gtol, k) for k in NAMES]:
+            if ref.size == 0:
+                continue
+            for fn, nrm in ((rel_err, 2), (rel_err_inf, np.inf)):
+                fl = None if gname is None else grad_floor(gname, np.float64(g[i])[None], sol["z"][None], norm=nrm)
+                e = fn(out[k][i][None], ref[None], fl)[0]
+                assert e <= tol, (i, k, nrm, e)
+    return st.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,extra,m,rank", [(20, 10, 3, 0), (40, 20, 0, 0), (30, 15, 5, 10),
+                                            (64, 32, 16, 0), (7, 5, 1, 2)])
+def test_psd_q_and_lp_match_oracle_fp32(n, extra, m, rank):
+    B = 6
+    batch = _batch([inputs.psd_qp(n, extra, m, rank, index=i) for i in range(B)])
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PSD)
+    bst = _run_and_compare(batch, g, np.float32, 1e-5, 1e-4, 1e-4)
+    assert ((bst & 0xff) == 0).all() and (bst & FLAG_REGULARIZED_Q).all()
+
+
+def test_psd_q_global_memory_path_and_fp64():
+    B = 4
+    batch = _batch([inputs.psd_qp(24, 12, 4, 0, index=50 + i) for i in range(B)])
+    g = inputs.upstream_grad(B, 24, workload=inputs.WL_PSD, start=50)
+    opts = default_options(torch.float32)
+    opts.path = 1
+    _run_and_compare(batch, g, np.float32, 1e-5, 1e-4, 1e-4, options=opts)
+    b64 = _batch([inputs.psd_qp(24, 12, 4, 3, index=60 + i, dtype=np.float64) for i in range(B)])
+    _run_and_compare(b64.astype(np.float64), g.astype(np.float64), np.float64, 1e-8, 1e-7, 1e-7)
+
+
+def test_tv_denoising_layer_matches_oracle():
+    """TV denoising (§4.2) of synthetic piecewise-constant signals, n = 24 (47 variables,
+    46 inequalities), loss = ‖z* − clean‖² through the denoised part."""
+    B, n = 8, 24
+    ys = [inputs.tv_signal(n, index=i) for i in range(B)]
+    batch = _batch([tuple(np.float32(x) for x in inputs.tv_qp(y, 0.2)) for y in ys]).astype(np.float32)
+    g = np.zeros((B, 2 * n - 1), dtype=np.float32)
+    g[:, :n] = inputs.upstream_grad(B, n, workload=inputs.WL_TV)
+    bst = _run_and_compare(batch, g, np.float32, 1e-5, 1e-4, 1e-4)
+    assert (bst & FLAG_REGULARIZED_Q).all()
+
+
+def test_positive_definite_q_is_not_regularised():
+    batch = inputs.random_batch(4, 20, 20, 5, workload=inputs.WL_PLAIN, start=700)
+    T = [torch.from_numpy(x).to(DEV) for x in (batch.Q, batch.q, batch.G, batch.h, batch.A, batch.b)]
+    fwd = qp_forward(*T)
+    st = torch.full((4,), -1, dtype=torch.int32, device=DEV)
+    qp_backward(fwd, torch.ones((4, 20), device=DEV), status=st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
