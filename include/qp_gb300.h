@@ -233,9 +233,10 @@ int qp_packed_plan_ex(const qp_options* opt, int dtype, int B, const int32_t* di
  * status/iters/resid indexed by instance id; workspace of sizes->ws_bytes bytes).  When a
  * batch holds both kinds, the global-path and shared-memory-path instances run as two
  * persistent kernels side by side: the global-path one first, on `stream`, the other on a
- * library-owned side stream forked from `stream` and joined back to it by events (created on
- * a device's first such call: make that call before any stream capture).  Its blocks take
- * SMs as the global-path blocks finish their queue. */
+ * library-owned side stream forked from `stream` and joined back to it by events (one side
+ * stream per caller stream, for up to 16 streams per device; created on a stream's first
+ * such call: make that call before any stream capture).  Its blocks take SMs as the
+ * global-path blocks finish their queue. */
 int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance_desc* desc,
                       const qp_packed_sizes* sizes, const void* Q, const void* q,
                       const void* G, const void* h, const void* A, const void* b, void* z,
@@ -287,6 +288,36 @@ const char* qp_strerror(int code);
  * Returns QP_OK, or QP_EINVAL for a negative count or null arrays. */
 int qp_host_copy_many(int count, void* const* dst, const void* const* src,
                       const size_t* bytes, int threads);
+
+/* Field rules of qp_host_pack / qp_host_unpack: the length and packed offset of one
+ * instance's array, from its descriptor (outputs share the rules of the inputs they are
+ * laid out like: z and ∂ℓ/∂z* like q, λ like h, ν like b, gradients like their inputs). */
+#define QP_FIELD_Q 0   /* n·n at oQ      */
+#define QP_FIELD_Q1 1  /* n at oq        */
+#define QP_FIELD_G 2   /* nineq·n at oG  */
+#define QP_FIELD_H 3   /* nineq at oh    */
+#define QP_FIELD_A 4   /* neq·n at oA    */
+#define QP_FIELD_B 5   /* neq at ob      */
+
+/* qp_host_pack -- host-side utility of the serving loop; the paper has no counterpart.
+ * Gathers per-instance HOST arrays into one packed HOST buffer laid out as the packed calls
+ * expect.  desc[B]: a plan from qp_packed_plan (any order; ids 0..B−1).  For each instance
+ * and each field f < nfields, copies src[id·nfields + f] (len elements of esz bytes, by rule
+ * fields[f]; a NULL source is skipped) to dst + (sec[f] + off)·esz, off the rule's packed
+ * offset.  sec[f] is the element offset of field f's section in dst.  Runs on up to
+ * `threads` host threads; touches no GPU state.  QP_EINVAL on bad arguments. */
+int qp_host_pack(int B, const qp_instance_desc* desc, int esz, int nfields,
+                 const int32_t* fields, const int64_t* sec, const void* const* src, void* dst,
+                 int threads);
+
+/* qp_host_unpack -- the inverse gather for results: reads field f of each instance from
+ * src + (sec[f] + off)·esz and writes instance id's fields contiguously, in field order, to
+ * dst + dst_off[id]·esz; fills dst_off[0..B] (dst_off[B] = total elements).  dst must hold
+ * dst_off[B] elements (at most B·Σ field lengths of the largest instance; callers size it
+ * from the plan totals: Σ_f sizes of the sections).  Host memory only. */
+int qp_host_unpack(int B, const qp_instance_desc* desc, int esz, int nfields,
+                   const int32_t* fields, const int64_t* sec, const void* src, void* dst,
+                   int64_t* dst_off, int threads);
 
 #ifdef __cplusplus
 }

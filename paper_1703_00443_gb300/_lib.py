@@ -106,6 +106,10 @@ EXPORTS = {
                         + [c_void_p] * 4 + [c_size_t] + [c_void_p] * 11),
     "qp_strerror": (ctypes.c_char_p, [c_int]),
     "qp_host_copy_many": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int]),
+    "qp_host_pack": (c_int, [c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                             c_void_p, c_int]),
+    "qp_host_unpack": (c_int, [c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_int]),
     "qp_forward_noalloc": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                            + [c_void_p] * 12 + [c_void_p]),
     "qp_packed_plan": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_void_p,

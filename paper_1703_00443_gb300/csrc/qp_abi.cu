@@ -125,33 +125,46 @@ Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
 
 static_assert(sizeof(qp_instance_desc) == sizeof(qpk::PackedDesc), "descriptor layout");
 
-// A non-blocking side stream and a fork/join event pair per device, created on first use (a
-// host-side resource, not device memory) and kept for the life of the process.
+// Non-blocking side streams, each with a fork/join event pair, created on first use (host-side
+// resources, not device memory) and kept for the life of the process.  A caller's stream
+// gets its own side stream (up to kSideSlots per device; beyond that, streams share slots by
+// hash), so packed calls issued on different streams do not queue behind one another.
 struct SideStream {
+  cudaStream_t owner = nullptr;   // the caller stream this slot serves
+  bool used = false;
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   std::mutex mu;
 };
+constexpr int kSideSlots = 16;
 
-SideStream* side_stream() {
+SideStream* side_stream(cudaStream_t owner) {
   static std::mutex mu;
-  static SideStream slots[64];
+  static SideStream slots[64][kSideSlots];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
     return nullptr;
   }
   std::lock_guard<std::mutex> lk(mu);
-  SideStream& x = slots[dev];
-  if (!x.s) {
-    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+  SideStream* row = slots[dev];
+  SideStream* x = nullptr;
+  for (int i = 0; i < kSideSlots && !x; ++i)
+    if (row[i].used && row[i].owner == owner) x = &row[i];
+  for (int i = 0; i < kSideSlots && !x; ++i)
+    if (!row[i].used) x = &row[i];
+  if (!x) x = &row[(reinterpret_cast<uintptr_t>(owner) >> 4) % kSideSlots];
+  if (!x->used) {
+    if (cudaStreamCreateWithFlags(&x->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->join, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
+    x->used = true;
+    x->owner = owner;
   }
-  return &x;
+  return x;
 }
 
 int num_sms() {
@@ -429,7 +442,7 @@ int qp_forward_packed(const qp_options* opt, int dtype, int B, const qp_instance
     // from `stream` and joined back to it.  Each block of either kernel holds its SM until its
     // queue runs dry, so as global-path blocks finish, shared-memory-path blocks take their
     // SMs: the hardware block scheduler balances the two queues without a fixed split.
-    SideStream* ss = side_stream();
+    SideStream* ss = side_stream(st);
     if (!ss) return QP_ECUDA;
     std::lock_guard<std::mutex> lk(ss->mu);
     if (cudaEventRecord(ss->fork, st) != cudaSuccess) return QP_ECUDA;

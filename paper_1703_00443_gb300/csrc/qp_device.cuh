@@ -407,6 +407,27 @@ __device__ __forceinline__ void block_reduce4f(float (&v)[4], float* red) {
   __syncthreads();
 }
 
+// Block-wide maximum of eight floats (NaN-propagating; all threads get the results); `red`
+// holds 8·NWARPS floats.
+__device__ __forceinline__ void block_reduce8f_max(float (&v)[8], float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = ropf<R_MAX>(v[k], __shfl_xor_sync(0xffffffffu, v[k], off));
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[8 * w + k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = red[k];
+#pragma unroll
+  for (int i = 1; i < NWARPS; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = ropf<R_MAX>(v[k], red[8 * i + k]);
+  __syncthreads();
+}
+
 template <int O0, int O1, int O2, int O3>
 __device__ __forceinline__ void block_reduce4(double (&v)[4], double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1951,6 +1972,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const Packed
   }
 }
 
+// One 16-byte streaming store (evict-first: the gradients are not read again here) of the
+// first 16 / sizeof(T) entries of v.
+__device__ __forceinline__ void st16_stream(float* o, const float (&v)[4]) {
+  __stcs(reinterpret_cast<float4*>(o), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void st16_stream(double* o, const double (&v)[4]) {
+  __stcs(reinterpret_cast<double2*>(o), make_double2(v[0], v[1]));
+}
+
 // ------------------------------------------------------------------ backward kernel
 template <typename T>
 __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm) {
@@ -2059,15 +2089,12 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   // blocks (d_z, d_ν, d̃_λ), the correction is below 1e-3·max(‖block‖∞, 1e-3·‖∂ℓ/∂z‖∞)
   // (at most P.refine steps).  Well-conditioned systems stop after the first step;
   // near-singular A Q⁻¹ Aᵀ blocks take more.
-  float gfloor;
-  {
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = tid; i < n; i += NTHREADS) v[0] = fmaxf(v[0], fabsf((float)gz[i]));
-    if (gl) for (int i = tid; i < p; i += NTHREADS) v[1] = fmaxf(v[1], fabsf((float)gl[i]));
-    if (gn) for (int i = tid; i < m; i += NTHREADS) v[2] = fmaxf(v[2], fabsf((float)gn[i]));
-    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
-    gfloor = 1e-3f * fmaxf(v[0], fmaxf(v[1], v[2]));
-  }
+  // This thread's part of max(‖∂ℓ/∂z‖∞, ‖∂ℓ/∂λ‖∞, ‖∂ℓ/∂ν‖∞), reduced with the first step's
+  // norms.
+  float gpart = 0.f, gfloor = 0.f;
+  for (int i = tid; i < n; i += NTHREADS) gpart = fmaxf(gpart, fabsf((float)gz[i]));
+  if (gl) for (int i = tid; i < p; i += NTHREADS) gpart = fmaxf(gpart, fabsf((float)gl[i]));
+  if (gn) for (int i = tid; i < m; i += NTHREADS) gpart = fmaxf(gpart, fabsf((float)gn[i]));
   for (int rs = 0; rs < P.refine; ++rs) {
     for (int i = tid; i < n + p + m; i += NTHREADS)
       xs[i] = Split<T>::make(i < n ? dz[i] : (i < n + p ? dlt[i - n] : dnu[i - n - p]));
@@ -2078,10 +2105,15 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
                  rz, rl, rn);
     for (int i = tid; i < m1; i += NTHREADS) u[i] = (i < n) ? (T)(-rz[i]) : (i < nz ? T(0) : (T)(-rn[i - nz]));
     __syncthreads();
-    if (!mv_rows_xreg<8>(SR, m1, m1 + p, m1, u, [&](int r, T val) { wv[r] = val; }))
-      mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, [&](int r, T val) { wv[r] = val; });
-    __syncthreads();
-    for (int i = tid; i < p; i += NTHREADS) rhs[i] = wv[m1 + i] + (T)rl[i];
+    {
+      // [S; RE]·u, with the right-hand side RE·u + ρ_λ of the Schur system formed as each
+      // row of RE·u lands
+      auto epi = [&](int r, T val) {
+        wv[r] = val;
+        if (r >= m1) rhs[r - m1] = val + (T)rl[r - m1];
+      };
+      if (!mv_rows_xreg<8>(SR, m1, m1 + p, m1, u, epi)) mv_rows<8>(SR, m1, m1 + p, m1, TRI_ALL, u, epi);
+    }
     __syncthreads();
     if (p > 0) {
       if (blk) blk_solve(p, X, p, rhs, y, dl, tscr);
@@ -2092,27 +2124,29 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
     if (p == 0)
       for (int i = tid; i < m1; i += NTHREADS) dzn[i] = wv[i];
     __syncthreads();
-    float v[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
+    // v[0..2]: the corrections' norms, v[3..5]: the updated blocks' norms, v[6]: the
+    // upstream gradient's norm (first step)
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, rs == 0 ? gpart : 0.f, 0.f};
     for (int i = tid; i < n; i += NTHREADS) {
       dz[i] += (double)dzn[i];
       v[0] = ropf<R_MAX>(v[0], fabsf((float)dzn[i]));
-      w[0] = ropf<R_MAX>(w[0], fabsf((float)dz[i]));
+      v[3] = ropf<R_MAX>(v[3], fabsf((float)dz[i]));
     }
     for (int i = tid; i < m; i += NTHREADS) {
       dnu[i] += (double)dzn[nz + i];
       v[1] = ropf<R_MAX>(v[1], fabsf((float)dzn[nz + i]));
-      w[1] = ropf<R_MAX>(w[1], fabsf((float)dnu[i]));
+      v[4] = ropf<R_MAX>(v[4], fabsf((float)dnu[i]));
     }
     for (int i = tid; i < p; i += NTHREADS) {
       dlt[i] += (double)dl[i];
       v[2] = ropf<R_MAX>(v[2], fabsf((float)dl[i]));
-      w[2] = ropf<R_MAX>(w[2], fabsf((float)dlt[i]));
+      v[5] = ropf<R_MAX>(v[5], fabsf((float)dlt[i]));
     }
-    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(v, red);
-    block_reduce4f<R_MAX, R_MAX, R_MAX, R_MAX>(w, red);
+    block_reduce8f_max(v, red);
+    if (rs == 0) gfloor = 1e-3f * v[6];
     bool done = true;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) done = done && (v[k] <= 1e-3f * fmaxf(w[k], gfloor));
+    for (int k = 0; k < 3; ++k) done = done && (v[k] <= 1e-3f * fmaxf(v[3 + k], gfloor));
     if (done || !isfinite(v[0] + v[1] + v[2])) break;
   }
 
@@ -2128,29 +2162,48 @@ __device__ __forceinline__ void bwd_body(const BwdInst<T>& P, unsigned char* sm)
   for (int i = tid; i < p; i += NTHREADS) { vl[i] = (T)lam[i]; vdl[i] = (T)dlt[i]; }
   for (int i = tid; i < m; i += NTHREADS) { vnu[i] = (T)nu[i]; vdnu[i] = (T)dnu[i]; }
   __syncthreads();
-  if (P.dQ) {
-    T* o = P.dQ;
-    for (int e = tid; e < n * n; e += NTHREADS) {
-      const int i = e / n, j = e - i * n;
-      o[e] = T(0.5) * fma(vdz[i], vz[j], vz[i] * vdz[j]);
+  // Rows of dQ (scale ½), dG and dA as one sequence of n + p + m rows of
+  // scale·(a_i z_jᵀ + c_i d_z,jᵀ); each thread keeps one 16-byte column group of z and d_z in
+  // registers and writes that group of every k-th row with one streaming store.
+  const int VW = 16 / (int)sizeof(T), nv = n / VW;
+  const bool vec = n % VW == 0 && nv <= NTHREADS &&
+      ((((uintptr_t)P.dQ) | ((uintptr_t)P.dG) | ((uintptr_t)P.dA)) & 15) == 0;
+  auto row_of = [&](int r, T*& o, T& a, T& c, T& sc) {
+    if (r < n) { o = P.dQ ? P.dQ + (size_t)r * n : nullptr; a = vdz[r]; c = vz[r]; sc = T(0.5); }
+    else if (r < n + p) {
+      const int i = r - n;
+      o = P.dG ? P.dG + (size_t)i * n : nullptr; a = vdl[i]; c = vl[i]; sc = T(1);
+    } else {
+      const int i = r - n - p;
+      o = P.dA ? P.dA + (size_t)i * n : nullptr; a = vdnu[i]; c = vnu[i]; sc = T(1);
+    }
+  };
+  if (vec) {
+    const int rpp = NTHREADS / nv, g = tid % nv, r0 = tid / nv;
+    if (r0 < rpp) {
+      T zj[4], dj[4];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) { zj[e] = vz[g * VW + e]; dj[e] = vdz[g * VW + e]; }
+      for (int r = r0; r < n + p + m; r += rpp) {
+        T* o; T a, c, sc;
+        row_of(r, o, a, c, sc);
+        if (!o) continue;
+        T v[4];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) v[e] = sc * fma(a, zj[e], c * dj[e]);
+        st16_stream(o + g * VW, v);
+      }
+    }
+  } else {
+    for (int r = 0; r < n + p + m; ++r) {
+      T* o; T a, c, sc;
+      row_of(r, o, a, c, sc);
+      if (o)
+        for (int j = tid; j < n; j += NTHREADS) o[j] = sc * fma(a, vz[j], c * vdz[j]);
     }
   }
   if (P.dq) for (int i = tid; i < n; i += NTHREADS) P.dq[i] = vdz[i];
-  if (P.dG) {
-    T* o = P.dG;
-    for (int e = tid; e < p * n; e += NTHREADS) {
-      const int i = e / n, j = e - i * n;
-      o[e] = fma(vdl[i], vz[j], vl[i] * vdz[j]);
-    }
-  }
   if (P.dh) for (int i = tid; i < p; i += NTHREADS) P.dh[i] = -vdl[i];
-  if (P.dA) {
-    T* o = P.dA;
-    for (int e = tid; e < m * n; e += NTHREADS) {
-      const int i = e / n, j = e - i * n;
-      o[e] = fma(vdnu[i], vz[j], vnu[i] * vdz[j]);
-    }
-  }
   if (P.db) for (int i = tid; i < m; i += NTHREADS) P.db[i] = -vdnu[i];
 }
 

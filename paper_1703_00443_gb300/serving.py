@@ -6,7 +6,7 @@ and the HBM budget covers the batch (workspace, packed inputs, outputs and gradi
 Requests wait in one queue per size class (by n, thresholds ``size_classes``) and a batch
 takes requests of one class, the class whose oldest request is oldest: a batch finishes
 with its largest instance, so small requests are not held back by large ones.  Each
-admitted batch runs forward and backward (one persistent launch each, ``packed.PackedBatch``)
+admitted batch runs forward and backward (``qp_forward_packed`` / ``qp_backward_packed``)
 on its own CUDA stream, so a batch admitted while others are running overlaps with them on
 the device; its iterates and factorisation stay in device memory between the two launches.
 When a batch's completion event fires, its results are copied to the host, every request's
@@ -14,11 +14,12 @@ future is resolved with its own z*, λ*, ν* and gradients, and the batch's slot
 released.  Latency is measured from each request's arrival to the resolution of its future.
 
 Each stream slot keeps one pinned host buffer for a batch's inputs and one for its results,
-grown on demand and reused: a batch is packed into sections of the input buffer with numpy
-slice copies and moves to the device in one copy, and all its results come back in one copy.
-The host copies (requests into the staging buffer, results out of it) go to the library's
-native ``qp_host_copy_many`` as one list per batch, which copies on a few host threads
-outside the interpreter lock.
+grown on demand and reused.  The per-batch host work runs in native calls that release the
+interpreter lock: ``qp_packed_plan_ex`` plans the batch, ``qp_host_pack`` gathers every
+request's arrays (and the descriptors) into the input buffer, which moves to the device in
+one copy; the results come back in one copy and ``qp_host_unpack`` scatters them into one
+host array per batch, each request's fields contiguous.  A request's future receives a
+read-only mapping whose arrays are views of that array, made on access.
 
 Each instance is solved by one thread block on the kernel path its own size selects, so a
 request's result does not depend on what it was batched with.
@@ -26,9 +27,11 @@ request's result does not depend on what it was batched with.
 from __future__ import annotations
 
 import collections
+import collections.abc
 import concurrent.futures
 import ctypes
 import dataclasses
+import itertools
 import threading
 import time
 
@@ -36,10 +39,46 @@ import numpy as np
 import torch
 
 from . import _lib
-from .packed import PackedBatch, PackedForward
-from .qp import default_options, workspace_bytes
+from .qp import QP_F32, QP_F64, QPError, _check, default_options, workspace_bytes
 
 GRAD_KEYS = ("dQ", "dq", "dG", "dh", "dA", "db")
+# Field rules of qp_host_pack / qp_host_unpack (QP_FIELD_* in the C header).
+F_Q, F_Q1, F_G, F_H, F_A, F_B = range(6)
+# inputs Q, q, G, h, A, b and dℓ/dz; results z, λ, ν and the six gradients
+FIELDS_IN = (F_Q, F_Q1, F_G, F_H, F_A, F_B, F_Q1)
+FIELDS_OUT = (F_Q1, F_H, F_B, F_Q, F_Q1, F_G, F_H, F_A, F_B)
+OUT_NAMES = ("z", "lam", "nu") + GRAD_KEYS
+
+
+class ServedResult(collections.abc.Mapping):
+    """Results of one request: z, lam, nu, the six gradients (views of the batch's result
+    array, made on access) and the forward status."""
+
+    __slots__ = ("_buf", "_off", "_dims", "status")
+
+    def __init__(self, buf, off, dims, status):
+        self._buf, self._off, self._dims, self.status = buf, int(off), dims, int(status)
+
+    def _shapes(self):
+        n, p, m = self._dims
+        return ((n,), (p,), (m,), (n, n), (n,), (p, n), (p,), (m, n), (m,))
+
+    def __getitem__(self, key):
+        if key == "status":
+            return self.status
+        o = self._off
+        for name, shp in zip(OUT_NAMES, self._shapes()):
+            size = int(np.prod(shp))
+            if name == key:
+                return self._buf[o:o + size].reshape(shp)
+            o += size
+        raise KeyError(key)
+
+    def __iter__(self):
+        return iter(OUT_NAMES + ("status",))
+
+    def __len__(self):
+        return len(OUT_NAMES) + 1
 
 
 @dataclasses.dataclass
@@ -95,16 +134,8 @@ class Admission:
         self.reserved -= int(nbytes)
 
 
-def _copy_many(dst, src, nbytes, threads):
-    """Host copies dst[i] <- src[i] (nbytes[i] bytes; integer addresses) in one native call."""
-    k = len(nbytes)
-    if k == 0:
-        return
-    lib = _lib.load()
-    rc = lib.qp_host_copy_many(k, (ctypes.c_void_p * k)(*dst), (ctypes.c_void_p * k)(*src),
-                               (ctypes.c_size_t * k)(*nbytes), int(threads))
-    if rc != 0:
-        raise RuntimeError(f"qp_host_copy_many failed: {rc}")
+_FIELDS_IN_C = (ctypes.c_int32 * 7)(*FIELDS_IN)
+_FIELDS_OUT_C = (ctypes.c_int32 * 9)(*FIELDS_OUT)
 
 
 def _sections(sizes, align=64):
@@ -206,87 +237,90 @@ class QPServer:
     # ------------------------------------------------------------------ scheduler
     def _launch(self, reqs, sidx):
         t0 = time.perf_counter()
+        lib = _lib.load()
         stream, stg = self.streams[sidx], self.staging[sidx]
-        dims = [r.dims for r in reqs]
-        keys = PackedBatch.KEYS
         ph = self.phase_s
+        B = len(reqs)
+        code = QP_F32 if self.dtype == torch.float32 else QP_F64
+        esz = 4 if self.dtype == torch.float32 else 8
+        dims = np.array([r.dims for r in reqs], dtype=np.int32)
+        desc = (_lib.QPInstanceDesc * B)()
+        sizes = _lib.QPPackedSizes()
+        _check(lib.qp_packed_plan_ex(ctypes.byref(self.options), code, B,
+                                     dims.ctypes.data_as(ctypes.c_void_p), None, None, desc,
+                                     ctypes.byref(sizes)))
+        t1 = time.perf_counter()
+        ph["plan"] += t1 - t0
+        tin = [sizes.nQ, sizes.nq, sizes.nG, sizes.nh, sizes.nA, sizes.nb, sizes.nq]
+        tout = [sizes.nq, sizes.nh, sizes.nb, sizes.nQ, sizes.nq, sizes.nG, sizes.nh, sizes.nA,
+                sizes.nb]
+        dbytes = B * ctypes.sizeof(_lib.QPInstanceDesc)
+        isec, n_in = _sections(tin + [(dbytes + esz - 1) // esz])
+        osec, n_out = _sections(tout)
+        stg.reserve(n_in, n_out, B)
+        # the descriptors travel in the same staging buffer, after the inputs
+        ctypes.memmove(stg.inp.data_ptr() + isec[7] * esz, desc, dbytes)
+        src = (ctypes.c_void_p * (7 * B))(*itertools.chain.from_iterable(r.ptrs for r in reqs))
+        _check(lib.qp_host_pack(B, desc, esz, 7, _FIELDS_IN_C, (ctypes.c_int64 * 8)(*isec), src,
+                                stg.inp.data_ptr(), self.copy_threads))
+        t2 = time.perf_counter()
+        ph["pack"] += t2 - t1
         with torch.cuda.stream(stream):
-            pb = PackedBatch(dims, dtype=self.dtype, device=self.device, options=self.options)
-            t1 = time.perf_counter()
-            ph["plan"] += t1 - t0
-            tot = pb.totals
-            # inputs: Q q G h A b and dℓ/dz; results: z λ ν and the six gradients
-            isec, n_in = _sections([tot[k] for k in keys] + [tot["q"]])
-            osec, n_out = _sections([tot["q"], tot["h"], tot["b"]] + [tot[k] for k in keys])
-            stg.reserve(n_in, n_out, len(reqs))
-            # gaps between instances are never read by the kernels
-            addr, esz = stg.inp.data_ptr(), stg.inp.element_size()
-            dst, src, nbytes = [], [], []
-            for j, key in enumerate(keys + ("q",)):
-                lens = pb.lengths[key]
-                keep = np.nonzero(lens)[0]
-                dst += (addr + (isec[j] + pb.offsets[key][keep]) * esz).tolist()
-                src += [reqs[i].ptrs[j] for i in keep.tolist()]   # C-contiguous (submit)
-                nbytes += (lens[keep] * esz).tolist()
-            tc = time.perf_counter()
-            ph["pack_lists"] += tc - t1
-            _copy_many(dst, src, nbytes, self.copy_threads)
-            gbase = isec[len(keys)]
-            t2 = time.perf_counter()
-            ph["pack_copy"] += t2 - tc
             dev_in = torch.empty(n_in, dtype=self.dtype, device=self.device)
             dev_in.copy_(stg.inp[:n_in], non_blocking=True)
-            view = lambda buf, off, n: buf[off:off + max(int(n), 1)]  # noqa: E731
-            Q, q, G, h, A, b = (view(dev_in, isec[j], tot[k]) for j, k in enumerate(keys))
-            g = view(dev_in, gbase, tot["q"])
-            dev_out = torch.zeros(n_out, dtype=self.dtype, device=self.device)
-            nB = max(len(reqs), 1)
-            fo = PackedForward(view(dev_out, osec[0], tot["q"]), view(dev_out, osec[1], tot["h"]),
-                               view(dev_out, osec[2], tot["b"]),
-                               torch.empty(nB, dtype=torch.int32, device=self.device),
-                               torch.empty(nB, dtype=torch.int32, device=self.device),
-                               torch.empty((nB, 4), dtype=torch.float64, device=self.device))
-            pb.forward(Q, q, G, h, A, b, out=fo)
-            grads = tuple(view(dev_out, osec[3 + j], tot[k]) for j, k in enumerate(keys))
-            pb.backward(Q, G, A, g, out=grads)
+            dev_out = torch.empty(n_out, dtype=self.dtype, device=self.device)
+            # status [B] and iters [B] (int32), then resid [B, 4] (FP64) 16-byte aligned
+            small = torch.empty(4 * ((3 * B + 3) // 4) + 8 * B, dtype=torch.int32,
+                                device=self.device)
+            ws = torch.empty(max(int(sizes.ws_bytes), 256), dtype=torch.uint8, device=self.device)
+            pi, po = dev_in.data_ptr(), dev_out.data_ptr()
+            a = [ctypes.c_void_p(pi + isec[k] * esz) if tin[k] else None for k in range(7)]
+            o = [ctypes.c_void_p(po + osec[k] * esz) if tout[k] else None for k in range(9)]
+            dsc = ctypes.c_void_p(pi + isec[7] * esz)
+            st_p = small.data_ptr()
+            status = ctypes.c_void_p(st_p)
+            iters = ctypes.c_void_p(st_p + 4 * B)
+            resid = ctypes.c_void_p(st_p + 4 * 4 * ((3 * B + 3) // 4))   # 16-byte aligned
+            sh = ctypes.c_void_p(stream.cuda_stream)
+            _check(lib.qp_forward_packed(ctypes.byref(self.options), code, B, dsc,
+                                         ctypes.byref(sizes), a[0], a[1], a[2], a[3], a[4], a[5],
+                                         o[0], o[1], o[2], status, iters, resid,
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), sh))
+            _check(lib.qp_backward_packed(ctypes.byref(self.options), code, B, dsc,
+                                          ctypes.byref(sizes), a[0], a[2], a[4],
+                                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), a[6],
+                                          o[3], o[4], o[5], o[6], o[7], o[8], None, sh))
             stg.out[:n_out].copy_(dev_out, non_blocking=True)
-            stg.status[:len(reqs)].copy_(fo.status[:len(reqs)], non_blocking=True)
+            stg.status[:B].copy_(small[:B], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
         t3 = time.perf_counter()
         ph["device"] += t3 - t2
         self.host_s["launch"] += t3 - t0
-        return {"reqs": reqs, "pb": pb, "osec": osec, "n_out": n_out, "event": ev, "stream": sidx,
-                "keep": (dev_in, dev_out, fo)}
+        return {"reqs": reqs, "desc": desc, "osec": osec, "n_out": n_out, "event": ev,
+                "stream": sidx, "keep": (dev_in, dev_out, small, ws)}
 
     def _retire(self, item):
         t0 = time.perf_counter()
-        pb, reqs, osec = item["pb"], item["reqs"], item["osec"]
+        lib = _lib.load()
+        reqs, osec = item["reqs"], item["osec"]
+        B = len(reqs)
         stg = self.staging[item["stream"]]
-        n_out = item["n_out"]
-        # one copy out of the staging buffer (in parallel ranges); each request's results view it
-        hout = np.empty(n_out, dtype=stg.out.numpy().dtype)
-        esz = hout.itemsize
-        step = (n_out + self.copy_threads - 1) // self.copy_threads
-        starts = range(0, n_out, step)
-        _copy_many([hout.ctypes.data + a * esz for a in starts],
-                   [stg.out.data_ptr() + a * esz for a in starts],
-                   [min(step, n_out - a) * esz for a in starts], self.copy_threads)
-        status = stg.status.numpy()
+        esz = stg.out.element_size()
+        hout = np.empty(item["n_out"], dtype=stg.out.numpy().dtype)
+        off = np.empty(B + 1, dtype=np.int64)
+        _check(lib.qp_host_unpack(B, item["desc"], esz, 9, _FIELDS_OUT_C,
+                                  (ctypes.c_int64 * 9)(*osec), ctypes.c_void_p(stg.out.data_ptr()),
+                                  hout.ctypes.data_as(ctypes.c_void_p),
+                                  off.ctypes.data_as(ctypes.c_void_p), self.copy_threads))
+        status = stg.status[:B].numpy().copy()
+        self.free_streams.append(item["stream"])   # the staging buffers are free again
         now = time.perf_counter()
-        fields = [("z", "q", osec[0]), ("lam", "h", osec[1]), ("nu", "b", osec[2])] + \
-            [(gk, k, osec[3 + j]) for j, (gk, k) in enumerate(zip(GRAD_KEYS, pb.KEYS))]
         for i, r in enumerate(reqs):
-            out = {}
-            for name, key, base in fields:
-                o, l = int(pb.offsets[key][i]), int(pb.lengths[key][i])
-                out[name] = hout[base + o:base + o + l].reshape(pb.shapes[key][i])
-            out["status"] = int(status[i])
             self.latencies.append(now - r.arrival)
-            r.future.set_result(out)
-        self.completed += len(reqs)
+            r.future.set_result(ServedResult(hout, off[i], r.dims, status[i]))
+        self.completed += B
         self.admission.release(sum(r.nbytes for r in reqs))
-        self.free_streams.append(item["stream"])
         self.host_s["retire"] += time.perf_counter() - t0
 
     def _loop(self):
