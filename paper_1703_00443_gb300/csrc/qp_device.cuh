@@ -626,6 +626,82 @@ __device__ __forceinline__ void ldg4_row(T (&v)[4], const T* row, int c0, int n,
   }
 }
 
+// The leading part of a split value: the FP32 rounding for T = float, the value itself for
+// T = double.
+__device__ __forceinline__ float split_hi(float2 v) { return v.x; }
+__device__ __forceinline__ double split_hi(double v) { return v; }
+
+// Row pass of the KKT operator, G x_z and A x_z, with x_z held in registers: lane gl of a row's
+// GL = 8 lanes keeps quads gl, gl+8, gl+16, gl+24 of x_z, so each element of a row costs one
+// load and one accumulation.  For 8 < ⌈n/4⌉ ≤ 32 (9 ≤ n ≤ 128); returns false, doing
+// nothing, otherwise.  FAST: plain T accumulation; else the double-float Acc.  The row loop
+// is uniform over the block, as the shuffles need.
+template <bool FAST, typename T, typename FL, typename FN>
+__device__ __forceinline__ bool kkt_rows_xreg(int n, int p, int m, const T* __restrict__ G,
+                                              const T* __restrict__ A,
+                                              const typename Split<T>::V* xv, bool vec,
+                                              FL add_l, FN add_n, double* out_l,
+                                              double* out_n) {
+  using V = typename Split<T>::V;
+  constexpr int GL = 8, NG = NTHREADS / GL, XQ = 4;
+  const int nq = (n + 3) / 4;
+  if (nq <= 8 || nq > GL * XQ) return false;
+  const int tid = threadIdx.x, g = tid / GL, gl = tid % GL;
+  V xr[XQ][4];
+#pragma unroll
+  for (int u = 0; u < XQ; ++u)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = 4 * (gl + u * GL) + c;
+      xr[u][c] = j < n ? xv[j] : V{};
+    }
+  for (int r0 = 0; r0 < p + m; r0 += NG) {
+    const int r = r0 + g;
+    const bool live = r < p + m;
+    const T* rowv = !live ? G : (r < p) ? G + (size_t)r * n : A + (size_t)(r - p) * n;
+    T av[XQ][4];
+#pragma unroll
+    for (int u = 0; u < XQ; ++u) {
+      const int q = gl + u * GL;
+      if (live && q < nq) {
+        ldg4_row(av[u], rowv, 4 * q, n, vec);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) av[u][c] = T(0);
+      }
+    }
+    double v;
+    if constexpr (FAST) {
+      T a0 = T(0), a1 = T(0);
+#pragma unroll
+      for (int u = 0; u < XQ; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c & 1) a1 = fma(av[u][c], split_hi(xr[u][c]), a1);
+          else a0 = fma(av[u][c], split_hi(xr[u][c]), a0);
+        }
+      T s = a0 + a1;
+#pragma unroll
+      for (int off = GL / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      v = (double)s;
+    } else {
+      Acc<T> acc;
+#pragma unroll
+      for (int u = 0; u < XQ; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc.add(av[u][c], xr[u][c]);
+#pragma unroll
+      for (int off = GL / 2; off > 0; off >>= 1) acc.shfl_merge(off);
+      v = acc.value();
+    }
+    if (live && gl == 0) {
+      if (r < p) out_l[r] = v + add_l(r);
+      else out_n[r - p] = v + add_n(r - p);
+    }
+  }
+  return true;
+}
+
 // FP64-accurate application of the (unreduced, slack-eliminated) KKT operator:
 //   out_z = Q x_z + Gᵀ x_λ + Aᵀ x_ν + add_z,  out_λ = G x_z + add_λ,  out_ν = A x_z + add_ν.
 // x = [x_z; x_λ; x_ν] is given split (FP32 hi/lo pairs for T = float).  Q is symmetric, so
@@ -680,9 +756,10 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restri
 #pragma unroll
     for (int c = 0; c < 4; ++c) scr[part * 4 * nq + 4 * jq + c] = acc[c];
   }
-  // Row pass: G x_z and A x_z with GL lanes per row (lane gl takes quads gl, gl+GL, ...),
-  // two rows per lane group at a time so that both rows' loads are in flight together.
-  {
+  // Row pass: G x_z and A x_z.  For 9 ≤ n ≤ 128 with x_z in registers (kkt_rows_xreg); else
+  // GL lanes per row (lane gl takes quads gl, gl+GL, ...), two rows per lane group at a time
+  // so that both rows' loads are in flight together.
+  if (!kkt_rows_xreg<false, T>(n, p, m, G, A, xv, vec, add_l, add_n, out_l, out_n)) {
     constexpr int GL = 8, NG = NTHREADS / GL, QB = 4;
     const int g = tid / GL, gl = tid % GL;
     for (int r0 = 0; r0 < p + m; r0 += 2 * NG) {
@@ -742,11 +819,6 @@ __device__ __forceinline__ void kkt_apply(int n, int p, int m, const T* __restri
   __syncthreads();
 }
 
-// The leading part of a split value: the FP32 rounding for T = float, the value itself for
-// T = double.
-__device__ __forceinline__ float split_hi(float2 v) { return v.x; }
-__device__ __forceinline__ double split_hi(double v) { return v; }
-
 // kkt_apply in plain T arithmetic (one FMA per matrix element, x rounded to T): the same
 // operator and the same quad/partial-sum organisation, with an error of order
 // n·2⁻²⁴·Σ|terms| for T = float instead of 2⁻⁴⁸.  The interior point loop uses it while μ
@@ -793,7 +865,7 @@ __device__ __forceinline__ void kkt_apply_fast(int n, int p, int m, const T* __r
 #pragma unroll
     for (int c = 0; c < 4; ++c) scr[part * 4 * nq + 4 * jq + c] = acc[c];
   }
-  {
+  if (!kkt_rows_xreg<true, T>(n, p, m, G, A, xv, vec, add_l, add_n, out_l, out_n)) {
     constexpr int GL = 8, NG = NTHREADS / GL, QB = 4;
     const int g = tid / GL, gl = tid % GL;
     for (int r0 = 0; r0 < p + m; r0 += 2 * NG) {
