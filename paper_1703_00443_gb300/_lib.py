@@ -18,8 +18,26 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqp_gb300.so")
 
-UNITS = ["qp_abi", "qp_fwd_f32", "qp_fwd_f64", "qp_bwd", "qp_noalloc", "qp_host"]
+SOURCES = ["qp_abi", "qp_fwd_f32", "qp_fwd_f64", "qp_bwd", "qp_noalloc", "qp_host", "qp_fwd_variant"]
 HEADERS = ["qp_device.cuh", "qp_launch.cuh", "qp_large.cuh"]
+
+
+def _variants():
+    """(object name, source, -D flags) of every forward-kernel variant: one object file each,
+    so that nvcc compiles them in parallel.  The (SW, CH) pairs match fwd_variant_exists()."""
+    out = []
+    for T, tag, pairs in (("float", "f32", [(1, 1), (2, 1), (4, 1), (4, 2)]),
+                          ("double", "f64", [(1, 1), (2, 1)])):
+        out.append((f"fwd_{tag}_large", "qp_fwd_variant", [f"-DQP_T={T}", "-DQP_KIND=1"]))
+        for kind, kname in ((0, "plain"), (2, "pksmem"), (3, "pkboth")):
+            for sw, ch in pairs:
+                out.append((f"fwd_{tag}_{kname}_{sw}{ch}", "qp_fwd_variant",
+                            [f"-DQP_T={T}", f"-DQP_KIND={kind}", f"-DQP_SW={sw}", f"-DQP_CH={ch}"]))
+    return out
+
+
+# (object name, source, extra flags); the variants go first, as they take longest
+UNITS = _variants() + [(u, u, []) for u in SOURCES if u != "qp_fwd_variant"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-Xptxas", "-v"]
@@ -34,7 +52,7 @@ def _nvcc() -> str:
 
 
 def _newest_input() -> float:
-    paths = [os.path.join(CSRC, u + ".cu") for u in UNITS]
+    paths = [os.path.join(CSRC, u + ".cu") for u in SOURCES]
     paths += [os.path.join(CSRC, h) for h in HEADERS]
     paths.append(os.path.join(INCLUDE, "qp_gb300.h"))
     return max(os.path.getmtime(p) for p in paths)
@@ -47,18 +65,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
 
-    def compile_unit(u):
-        src = os.path.join(CSRC, u + ".cu")
-        obj = os.path.join(BUILD, u + ".o")
-        log = os.path.join(BUILD, u + ".ptxas.log")
+    def compile_unit(unit):
+        name, source, defs = unit
+        src = os.path.join(CSRC, source + ".cu")
+        obj = os.path.join(BUILD, name + ".o")
+        log = os.path.join(BUILD, name + ".ptxas.log")
         with open(log, "w") as fh:
-            r = subprocess.run([nvcc, *NVCC_FLAGS, "-c", src, "-o", obj], stdout=fh,
+            r = subprocess.run([nvcc, *NVCC_FLAGS, *defs, "-c", src, "-o", obj], stdout=fh,
                                stderr=subprocess.STDOUT)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {u}.cu; see {log}:\n" + open(log).read()[-4000:])
+            raise RuntimeError(f"nvcc failed for {name} ({source}.cu); see {log}:\n"
+                               + open(log).read()[-4000:])
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    with ThreadPoolExecutor(max_workers=max(1, min(len(UNITS), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_unit, UNITS))
     tmp = LIB + ".tmp"
     r = subprocess.run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp,

@@ -1,40 +1,24 @@
-// FP64 forward-kernel variants (everything in FP64).
+// FP64 forward-kernel dispatch (everything in FP64).  The kernels themselves are compiled
+// one variant per object file from qp_fwd_variant.cu.
 #include "qp_launch.cuh"
 
 namespace qpk {
 
-template <int SW, int CH>
-static cudaError_t go(const FwdParams<double>& P, size_t smem, cudaStream_t st) {
-  auto k = qp_fwd_kernel<double, SW, CH>;
-  cudaError_t e = prepare_smem(k, smem);
-  if (e != cudaSuccess) return e;
-  k<<<P.B, NTHREADS, smem, st>>>(P);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_fwd_f64(const FwdParams<double>& P, int SW, int CH, size_t smem, cudaStream_t st) {
-  if (SW == 1 && CH == 1) return go<1, 1>(P, smem, st);
-  if (SW == 2 && CH == 1) return go<2, 1>(P, smem, st);
+  if (SW == 1 && CH == 1) return launch_fwd_v<double, 1, 1>(P, smem, st);
+  if (SW == 2 && CH == 1) return launch_fwd_v<double, 2, 1>(P, smem, st);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fwd_large_f64(const FwdParams<double>& P, size_t smem, cudaStream_t st) {
-  auto k = qp_fwd_large_kernel<double>;
-  cudaError_t e = prepare_smem(k, smem);
-  if (e != cudaSuccess) return e;
-  k<<<P.B, NTHREADS, smem, st>>>(P);
-  return cudaGetLastError();
+  return launch_fwd_large_v<double>(P, smem, st);
 }
 
 template <int SW, int CH>
 static cudaError_t gop(const PackedFwdParams<double>& P, size_t smem, int grid, int mode,
                        cudaStream_t st) {
-  auto k = mode == PK_BOTH ? qp_fwd_packed_kernel<double, SW, CH, PK_BOTH>
-                           : qp_fwd_packed_kernel<double, SW, CH, PK_SMEM>;
-  cudaError_t e = prepare_smem(k, smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, NTHREADS, smem, st>>>(P);
-  return cudaGetLastError();
+  return mode == PK_BOTH ? launch_fwd_packed_v<double, SW, CH, PK_BOTH>(P, smem, grid, st)
+                         : launch_fwd_packed_v<double, SW, CH, PK_SMEM>(P, smem, grid, st);
 }
 
 cudaError_t launch_fwd_packed_f64(const PackedFwdParams<double>& P, int SW, int CH, size_t smem,

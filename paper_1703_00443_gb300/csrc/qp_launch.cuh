@@ -16,6 +16,16 @@ namespace qpk {
 // up to SW·512 (resp. CH·512) lower-triangular tiles.
 bool fwd_variant_exists(int esz, int SW, int CH);
 
+// Each forward-kernel variant is compiled in an object file of its own (qp_fwd_variant.cu,
+// built once per variant with -DQP_T/-DQP_SW/-DQP_CH/-DQP_KIND), so the variants compile in
+// parallel; the dispatch functions below pick one at run time.
+template <typename T, int SW, int CH>
+cudaError_t launch_fwd_v(const FwdParams<T>& P, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fwd_large_v(const FwdParams<T>& P, size_t smem, cudaStream_t st);
+template <typename T, int SW, int CH, int MODE>
+cudaError_t launch_fwd_packed_v(const PackedFwdParams<T>& P, size_t smem, int grid, cudaStream_t st);
+
 cudaError_t launch_fwd_f32(const FwdParams<float>& P, int SW, int CH, size_t smem, cudaStream_t st);
 cudaError_t launch_fwd_f64(const FwdParams<double>& P, int SW, int CH, size_t smem, cudaStream_t st);
 cudaError_t launch_fwd_large_f32(const FwdParams<float>& P, size_t smem, cudaStream_t st);

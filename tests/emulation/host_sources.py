@@ -44,4 +44,25 @@ def generate(out):
         path = os.path.join(out, f.replace(".cu", ".cpp"))
         open(path, "w").write(s)
         units.append(path)
+    # the forward-kernel variants: one host unit per variant, as the library builds them
+    var = open(os.path.join(SRC, "qp_fwd_variant.cu")).read().replace(
+        "#include <cuda_runtime.h>", '#include "rt_shim.h"')
+    var = pat.sub(r"emu_launch(\1, \2, \3, \5);", var)
+    if "<<<" in var:
+        raise RuntimeError("unconverted launch in qp_fwd_variant.cu")
+    for name, _src, defs in variants():
+        head = "".join("#define " + d[2:].replace("=", " ", 1) + "\n" for d in defs)
+        path = os.path.join(out, name + ".cpp")
+        open(path, "w").write(head + var)
+        units.append(path)
     return units
+
+
+def variants():
+    """The library's list of forward-kernel variants (read from its build script)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "qp_lib_build", os.path.join(SRC, "..", "_lib.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod._variants()

@@ -43,7 +43,7 @@ def driver():
         if r.returncode:
             raise RuntimeError(r.stderr[-4000:])
         return obj
-    with ThreadPoolExecutor(5) as ex:
+    with ThreadPoolExecutor(os.cpu_count() or 4) as ex:
         objs = list(ex.map(cc, units + [os.path.join(EMU, "driver.cpp")]))
     exe = os.path.join(BUILD, "driver")
     r = subprocess.run(["g++", "-fsanitize=address", *objs, "-o", exe, "-lpthread"],
