@@ -114,6 +114,15 @@ int qp_supported(int dtype, int n, int nineq, int neq);
  * workspace, L2-resident), 0 if on the shared-memory kernel, −1 on invalid arguments. */
 int qp_uses_global_path(int dtype, int n, int nineq, int neq);
 
+/* 1 if qp_forward's setup factorisation of this size (§3.1: the blocks of the KKT matrix that
+ * do not change over the iterations, factored once) runs its rank-64 updates on the tensor
+ * cores (tcgen05, TF32 with a three-term split that keeps FP32 accuracy): FP32 instances on
+ * the global-memory kernel with n + neq ≥ 128 (after padding) whose operand tiles fit in
+ * shared memory.  0 otherwise (the CUDA-core sweep), −1 on invalid arguments.  `opt` may be
+ * NULL (automatic path) or force the path as qp_forward would.  The packed entry points
+ * always use the CUDA-core sweep. */
+int qp_uses_tensor_cores(const qp_options* opt, int dtype, int n, int nineq, int neq);
+
 /*
  * qp_forward -- batched primal-dual interior point solve (§3.1: slack form, affine
  * predictor Eq. 9, centering-plus-corrector Eq. 10, symmetrised and block-eliminated KKT

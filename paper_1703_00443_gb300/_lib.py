@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqp_gb300.so")
 
 SOURCES = ["qp_abi", "qp_fwd_f32", "qp_fwd_f64", "qp_bwd", "qp_noalloc", "qp_host", "qp_fwd_variant"]
-HEADERS = ["qp_device.cuh", "qp_launch.cuh", "qp_large.cuh"]
+HEADERS = ["qp_device.cuh", "qp_launch.cuh", "qp_large.cuh", "qp_tc.cuh"]
 
 
 def _variants():
@@ -118,6 +118,7 @@ EXPORTS = {
     "qp_workspace_bytes_opt": (c_size_t, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]),
     "qp_supported": (c_int, [c_int, c_int, c_int, c_int]),
     "qp_uses_global_path": (c_int, [c_int, c_int, c_int, c_int]),
+    "qp_uses_tensor_cores": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int]),
     "qp_forward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]
                    + [c_void_p] * 13 + [c_size_t, c_void_p]),
     "qp_backward": (c_int, [ctypes.POINTER(QPOptions), c_int, c_int, c_int, c_int, c_int]

@@ -87,7 +87,9 @@ struct Plan {
 };
 
 // force: 0 automatic, 1 global-memory path, 2 shared-memory path (ok = false if impossible).
-Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
+// packed: the instance runs in the persistent packed kernel (no tensor-core sweep, so no
+// panel-tile region in its workspace).
+Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0, bool packed = false) {
   Plan pl;
   const size_t lim = (size_t)max_smem_optin();
   int sw = 0, ch = 0;
@@ -115,7 +117,7 @@ Plan make_plan(int dtype, int n, int nineq, int neq, int force_global = 0) {
     }
   }
   qpk::WsLayout W;
-  W.init(n, pl.nz, nineq, neq, dtype == QP_F32 ? 4 : 8, pl.large);
+  W.init(n, pl.nz, nineq, neq, dtype == QP_F32 ? 4 : 8, pl.large, !packed);
   pl.ws = W.inst;
   pl.ok = pl.fsmem <= lim && pl.bsmem <= lim;
   return pl;
@@ -231,6 +233,13 @@ int qp_uses_global_path(int dtype, int n, int nineq, int neq) {
   return make_plan(dtype, n, nineq, neq).large ? 1 : 0;
 }
 
+int qp_uses_tensor_cores(const qp_options* opt, int dtype, int n, int nineq, int neq) {
+  if ((dtype != QP_F32 && dtype != QP_F64) || !dims_ok(1, n, nineq, neq)) return -1;
+  const Plan pl = make_plan(dtype, n, nineq, neq, opt ? opt->path : 0);
+  if (!pl.ok) return -1;
+  return pl.large && qpk::tc_sweep_ok(n, pl.nz, nineq, neq, dtype == QP_F32 ? 4 : 8) ? 1 : 0;
+}
+
 int qp_forward(const qp_options* opt, int dtype, int B, int n, int nineq, int neq,
                const void* Q, const void* q, const void* G, const void* h, const void* A,
                const void* b, void* z, void* lam, void* nu, int32_t* status, int32_t* iters,
@@ -343,7 +352,7 @@ int qp_packed_plan_ex(const qp_options* opt, int dtype, int B, const int32_t* di
     if (!dims_ok(1, n, p, m)) return QP_EINVAL;
     const int hint = path_hint ? path_hint[i] : 0;
     if (hint < 0 || hint > 2) return QP_EINVAL;
-    const Plan pl = make_plan(dtype, n, p, m, hint ? hint : o.path);
+    const Plan pl = make_plan(dtype, n, p, m, hint ? hint : o.path, true);
     if (!pl.ok) return QP_EUNSUPPORTED;
     qp_instance_desc& d = desc[i];
     d.n = n; d.nineq = p; d.neq = m; d.id = i; d.nz = pl.nz; d.flags = pl.large ? 1 : 0;

@@ -81,6 +81,30 @@ __host__ __device__ inline int32_t stamp_hash(const void* Q, const void* G, cons
 }
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+}  // namespace qpk
+
+#include "qp_tc.cuh"
+
+namespace qpk {
+
+// Shared memory of the global-memory forward kernel after its work region: the FP64 and
+// split vectors, the FP32 vectors and the reduction scratch (FwdSmem: odbl .. total).
+__host__ __device__ inline size_t large_tail_bytes(int n, int p, int m, int m1, size_t es) {
+  const size_t p4 = (size_t)(p + 3) / 4 * 4;
+  return align_up(8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16) +
+         align_up(8 * ((size_t)n + p + m), 16) + align_up(es * (3 * (size_t)m1 + 12 * p4), 16) +
+         align_up(8 * 4 * NWARPS, 16);
+}
+
+// Whether the global-memory path runs the setup sweep's rank-64 updates on the tensor cores
+// (qp_tc.cuh): FP32, at least two 64-pivot superblocks, and the operand tiles fit in the
+// shared work region next to the vectors.  A pure function of the sizes, so the workspace
+// layout, the shared-memory size and the kernel agree.
+__host__ __device__ inline bool tc_sweep_ok(int n, int nz, int p, int m, int esz) {
+  const int m1 = nz + m;
+  return esz == 4 && m1 >= TC_MIN_M1 &&
+         TC_SMEM_BYTES + large_tail_bytes(n, p, m, m1, 4) <= TC_SMEM_CAP;
+}
 
 // Number of primal variables after padding: 0-3 decoupled dummy variables (Q = 1 on the
 // diagonal, no constraint coupling) make n + neq a multiple of 4, so the pivot blocks of
@@ -98,15 +122,18 @@ __host__ __device__ inline int padded_nz(int n, int m) { return n + ((4 - (n + m
 // path appends diag(M), its Cholesky work matrix (row stride round4(p)) and its panel
 // scratch (the sweep's two 16-row panels, or the Cholesky's panel and staging buffer).
 struct WsLayout {
-  size_t oSR, oX, oIt, oSt, odM, oAw, oPan, inst;
-  __host__ __device__ void init(int n, int nz, int p, int m, int esz, bool large) {
+  size_t oSR, oX, oIt, oSt, odM, oAw, oPan, oTc, inst;
+  // tc_region: room for the tensor-core sweep's panel tiles where the size takes that sweep
+  // (the fixed-size global-memory kernel; the packed kernels use the CUDA-core sweep).
+  __host__ __device__ void init(int n, int nz, int p, int m, int esz, bool large,
+                                bool tc_region = true) {
     const size_t m1 = (size_t)nz + m;
     oSR = 0;
     oX = align_up(oSR + (m1 + p) * m1 * esz, 256);
     oIt = align_up(oX + (size_t)p * p * esz, 256);
     oSt = align_up(oIt + 8 * ((size_t)n + 2 * (size_t)p + m), 256);
     size_t o = align_up(oSt + 32, 256);
-    odM = oAw = oPan = o;
+    odM = oAw = oPan = oTc = o;
     if (large) {
       const size_t N = m1 + p, ldp = (N + 7) / 8 * 8;
       odM = o;  o = align_up(o + (size_t)p * esz, 256);
@@ -114,6 +141,9 @@ struct WsLayout {
       const size_t span = 2 * 16 * ldp;
       oAw = o;  o = align_up(o + (size_t)p * ((p + 3) & ~3) * esz, 256);
       oPan = o; o = align_up(o + (span > cpan ? span : cpan) * esz, 256);
+      oTc = o;
+      if (tc_region && tc_sweep_ok(n, nz, p, m, esz))
+        o = align_up(o + tc_panel_bytes((int)m1, p), 256);
     }
     inst = o;
   }
@@ -122,7 +152,7 @@ struct WsLayout {
 // Dynamic shared memory of the forward kernel.
 template <typename T>
 struct FwdSmem {
-  int nz, m1, N3, ldS, ldM, NT3, NTp, pan_smem, span_smem;
+  int nz, m1, N3, ldS, ldM, NT3, NTp, pan_smem, span_smem, tc_sweep;
   size_t oSR, oMb, odM, ocb, cbytes, odbl, osplit, ovec, ored, total;
   // large: S/RE, M/X and diag(M) live in the global workspace, only vectors and a work
   // region stay in shared memory.
@@ -162,12 +192,9 @@ struct FwdSmem {
       }
       cbytes = align_up(c, 16);
     }
-    pan_smem = span_smem = 0;
+    pan_smem = span_smem = tc_sweep = 0;
     const size_t p4 = (size_t)(p + 3) / 4 * 4;
-    const size_t tail = align_up(8 * (3 * (size_t)n + 4 * (size_t)p + 3 * (size_t)m), 16) +
-                        align_up(8 * ((size_t)n + p + m), 16) +
-                        align_up(es * (3 * (size_t)m1 + 12 * p4), 16) +
-                        align_up(8 * 4 * NWARPS, 16);
+    const size_t tail = large_tail_bytes(n, p, m, m1, es);
     if (large) {
       // The Cholesky panel and staging buffer (pivot scratch plus 2·chol_nb rows of ld
       // round8(p)) go to the work region when the whole layout stays within
@@ -184,6 +211,11 @@ struct FwdSmem {
       if (o + (sc > cbytes ? sc : cbytes) + tail <= LARGE_PANEL_SMEM_CAP) {
         span_smem = 1;
         if (sc > cbytes) cbytes = sc;
+      }
+      // The tensor-core sweep stages its operand tiles in the work region.
+      if (tc_sweep_ok(n, nz, p, m, (int)es)) {
+        tc_sweep = 1;
+        if (TC_SMEM_BYTES > cbytes) cbytes = align_up(TC_SMEM_BYTES, 16);
       }
     }
     o += cbytes;
@@ -1938,14 +1970,17 @@ __device__ __forceinline__ void fwd_smem_path(const FwdInst<T>& I, unsigned char
       [&](const T* rhs, T* y, T* out, T* scr) { chol_solve(p, Mb, L.ldM, rhs, y, out, scr); });
 }
 
-// One instance on the global-memory path (factors in the workspace, see qp_large.cuh).
-template <typename T>
+// One instance on the global-memory path (factors in the workspace, see qp_large.cuh).  TC:
+// whether the setup sweep may take its rank-64 updates on the tensor cores (qp_tc.cuh).  The
+// fixed-size kernel does; the persistent packed kernel does not (its tensor-core variant raised
+// a GPU fault whose cause was not found), so its workspace has no panel-tile region.
+template <typename T, bool TC>
 __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned char* sm) {
   FwdSmem<T> L;
   L.init(I.n, I.nz, I.p, I.m, true);
   const int n = I.n, p = I.p, m = I.m, nz = I.nz;
   WsLayout W;
-  W.init(n, nz, p, m, (int)sizeof(T), true);
+  W.init(n, nz, p, m, (int)sizeof(T), true, TC);
   T* SR = reinterpret_cast<T*>(I.ws + W.oSR);
   T* Mb = reinterpret_cast<T*>(I.ws + W.oX);
   T* dM = reinterpret_cast<T*>(I.ws + W.odM);
@@ -1956,7 +1991,8 @@ __device__ __forceinline__ void fwd_global_path(const FwdInst<T>& I, unsigned ch
   fwd_body<T>(I, L, sm, SR, Mb, p > 0 ? p : 1, dM, true,
       [&](const T* Qb, const T* Ab, const T* Gb, T delta, T zthr) {
         return gsweep_setup<T>(n, nz, p, m, Qb, Ab, Gb, SR, Mb, dM, pan, L.span_smem != 0, cb,
-                               delta, zthr);
+                               delta, zthr,
+                               TC && L.tc_sweep ? reinterpret_cast<T*>(I.ws + W.oTc) : nullptr);
       },
       [&](const T* dsh) {
         // Small Schur complements: the register-tile routine (M read from and X written to
@@ -1986,7 +2022,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_kernel(const FwdParams<T> 
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_large_kernel(const FwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char sm[];
-  fwd_global_path<T>(fixed_inst(P, blockIdx.x), sm);
+  fwd_global_path<T, true>(fixed_inst(P, blockIdx.x), sm);
 }
 
 // Packed batch of uneven sizes, persistent: blocks take instances from an atomic counter in
@@ -2035,7 +2071,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) qp_fwd_packed_kernel(const Packed
         if (I.status) *I.status = ST_NUM;
       }
     } else if constexpr (MODE == PK_BOTH) {
-      if (glob) fwd_global_path<T>(I, sm);
+      if (glob) fwd_global_path<T, false>(I, sm);
       else fwd_smem_path<T, SW, CH>(I, sm);
     } else {
       fwd_smem_path<T, SW, CH>(I, sm);

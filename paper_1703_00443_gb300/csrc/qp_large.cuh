@@ -34,7 +34,7 @@ template <typename T>
 __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* __restrict__ Q,
                                           const T* __restrict__ A, const T* __restrict__ G,
                                           T* SR, T* Mb, T* dM, T* pan, bool pan_in_sm, T* sm,
-                                          T delta, T zthr) {
+                                          T delta, T zthr, T* tcp) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m1 = nz + m, N = m1 + p, ldS = m1, ldM = p > 0 ? p : 1;
   const bool mvec = (p & 3) == 0;   // rows of Mb 16-byte aligned
@@ -55,7 +55,21 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
 
   const int RT = (N + 7) >> 3, CT = m1 >> 2;           // tiles of the SR region
   const int RTp = (p + 7) >> 3, CTp = (p + 3) >> 2;    // tile rows / columns of the λλ block
-  for (int k0 = 0; k0 < m1; k0 += LNB) {
+  int kstart = 0;
+#if defined(__CUDA_ARCH__) || defined(QP_HOST_EMULATION)
+  if constexpr (sizeof(T) == 4) {
+    // FP32 with the workspace's panel tiles: whole 64-pivot superblocks on the tensor cores,
+    // the remaining 16-pivot blocks below.
+    if (tcp != nullptr) {
+      const int nsb = m1 / TC_KB;
+      if (!tc_sweep_superblocks(n, nz, p, m, nsb, SR, Mb, ldM, dM, tcp,
+                                reinterpret_cast<unsigned char*>(sm), zthr))
+        return false;
+      kstart = nsb * TC_KB;
+    }
+  }
+#endif
+  for (int k0 = kstart; k0 < m1; k0 += LNB) {
     // Phase A (warp 0): scalar sweeps of the pivot block, recording r_k.
     if (warp == 0) {
       for (int e = lane; e < LNB * LNB; e += 32)

@@ -123,6 +123,14 @@ def uses_global_path(dtype, n, nineq, neq) -> bool:
     return lib.qp_uses_global_path(QP_F32 if dtype == torch.float32 else QP_F64, n, nineq, neq) == 1
 
 
+def uses_tensor_cores(dtype, n, nineq, neq, options=None) -> bool:
+    """Whether the setup factorisation of this size runs on the tensor cores."""
+    lib = _lib.load()
+    opt = ctypes.byref(options) if options is not None else None
+    return lib.qp_uses_tensor_cores(opt, QP_F32 if dtype == torch.float32 else QP_F64,
+                                    n, nineq, neq) == 1
+
+
 def qp_forward(Q, q, G=None, h=None, A=None, b=None, *, options=None, workspace=None,
                out=None) -> ForwardResult:
     """Solve the batch (C ABI ``qp_forward``) on the current CUDA stream."""

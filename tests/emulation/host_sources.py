@@ -13,7 +13,7 @@ def generate(out):
     dev = open(os.path.join(SRC, "qp_device.cuh")).read()
     large = open(os.path.join(SRC, "qp_large.cuh")).read()
     dev = dev.replace('#include "qp_large.cuh"', large.replace("#pragma once", ""))
-    dev = dev.replace("#include <cuda_runtime.h>", '#include "rt_shim.h"')
+    dev = dev.replace("#include <cuda_runtime.h>", '#define QP_HOST_EMULATION 1\n#include "rt_shim.h"')
     subs = [
         ('asm volatile("prefetch.global.L2 [%0];" :: "l"(c + o));', '(void)(c + o);'),
         ('asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(s), "l"(src) : "memory");',
@@ -31,6 +31,16 @@ def generate(out):
     dev = re.sub(r"\b__shared__\b", "static", dev)   # one block at a time: statics are per block
     dev = dev.replace("__stcs(", "emu_stcs(")
     open(os.path.join(out, "qp_device.cuh"), "w").write(dev)
+    # the tensor-core routines are device-only (under __CUDA_ARCH__); the host build takes
+    # the header for its layout functions and runs the CUDA-core sweep
+    tc = open(os.path.join(SRC, "qp_tc.cuh")).read()
+    tc = re.sub(r"#if defined\(__CUDA_ARCH__\)\n.*?#endif  // __CUDA_ARCH__\n", "", tc, flags=re.S)
+    if "asm" in re.sub(r"//.*", "", tc):
+        raise RuntimeError("inline assembly left in qp_tc.cuh")
+    # the wrappers' host definitions come before the routine that uses them
+    tc = tc.replace("// Bounded wait for the completion", '}  // namespace qpk\n#include "tc_emu.h"\n'
+                    "namespace qpk {\n// Bounded wait for the completion", 1)
+    open(os.path.join(out, "qp_tc.cuh"), "w").write(tc)
     lau = open(os.path.join(SRC, "qp_launch.cuh")).read()
     open(os.path.join(out, "qp_launch.cuh"), "w").write(
         lau.replace("#include <cuda_runtime.h>", '#include "rt_shim.h"'))

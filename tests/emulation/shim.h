@@ -87,6 +87,7 @@ inline long long min(long long a, long long b) { return a < b ? a : b; }
 inline size_t max(size_t a, size_t b) { return a > b ? a : b; }
 inline size_t min(size_t a, size_t b) { return a < b ? a : b; }
 inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+inline int atomicExch(int* p, int v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
 inline size_t __cvta_generic_to_shared(const void* p) { return (size_t)p; }
 inline unsigned long long emu_time_ns() {
   return (unsigned long long)std::chrono::duration_cast<std::chrono::nanoseconds>(

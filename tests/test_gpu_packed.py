@@ -48,27 +48,33 @@ def test_packed_equals_each_instance_alone():
     pb, res = _solve_packed(sizes, inst, gin)
     assert pb.n_global >= 1 and pb.n_global < len(sizes)   # both kernel paths in one launch
     assert (res["status"] == 0).all()
-    for i, t in enumerate(inst):
-        T = [torch.from_numpy(np.float32(x)).unsqueeze(0).to(DEV) for x in t]
-        f = qp_forward(*T)
-        g = qp_backward(f, torch.from_numpy(np.float32(gin[i])).unsqueeze(0).to(DEV))
-        torch.cuda.synchronize()
-        assert torch.equal(f.z[0], res["z"][i]), i
-        assert torch.equal(f.lam[0], res["lam"][i]), i
-        for k, gg in zip(NAMES, g):
-            assert torch.equal(gg[0], res[k][i]), (i, k)
+    _assert_equal_alone(inst, gin, res, np.float32)
+
+
+def _alone(t, g, npdt):
+    """The instance solved alone: by qp_forward/qp_backward, or, for sizes whose fixed-size
+    setup sweep takes the tensor cores (the packed kernels sweep on CUDA cores), as a packed
+    batch of one."""
+    from paper_1703_00443_gb300.qp import uses_tensor_cores
+    n, p, m = t[0].shape[0], t[2].shape[0], t[4].shape[0]
+    dtype = torch.float32 if npdt == np.float32 else torch.float64
+    if uses_tensor_cores(dtype, n, p, m):
+        _, r = _solve_packed([(n, p, m)], [t], [g], dtype=dtype)
+        return {k: r[k][0] for k in ("z", "lam") + NAMES}
+    T = [torch.from_numpy(npdt(x)).unsqueeze(0).to(DEV) for x in t]
+    f = qp_forward(*T)
+    gr = qp_backward(f, torch.from_numpy(npdt(g)).unsqueeze(0).to(DEV))
+    torch.cuda.synchronize()
+    out = {"z": f.z[0], "lam": f.lam[0]}
+    out.update({k: gg[0] for k, gg in zip(NAMES, gr)})
+    return out
 
 
 def _assert_equal_alone(inst, gin, res, npdt):
     for i, t in enumerate(inst):
-        T = [torch.from_numpy(npdt(x)).unsqueeze(0).to(DEV) for x in t]
-        f = qp_forward(*T)
-        g = qp_backward(f, torch.from_numpy(npdt(gin[i])).unsqueeze(0).to(DEV))
-        torch.cuda.synchronize()
-        assert torch.equal(f.z[0], res["z"][i]), i
-        assert torch.equal(f.lam[0], res["lam"][i]), i
-        for k, gg in zip(NAMES, g):
-            assert torch.equal(gg[0], res[k][i]), (i, k)
+        a = _alone(t, gin[i], npdt)
+        for k in ("z", "lam") + NAMES:
+            assert torch.equal(a[k], res[k][i]), (i, k)
 
 
 def test_packed_shared_memory_only_batch_equals_alone():

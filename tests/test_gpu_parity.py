@@ -296,3 +296,26 @@ def test_global_memory_kernel_large_sizes(n, nineq, neq):
     out = _run(batch, g, np.float32)
     assert (out["status"] == 0).all(), out["status"]
     _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)
+
+
+@pytest.mark.parametrize("n,nineq,neq,path", [(100, 60, 44, 1), (100, 100, 50, 1), (96, 37, 32, 1),
+                                              (140, 200, 30, 0), (150, 90, 37, 0),
+                                              (180, 70, 60, 1), (150, 0, 40, 1),
+                                              (200, 201, 17, 0)])
+def test_tensor_core_setup_sweep(n, nineq, neq, path):
+    """FP32 sizes whose fixed-size setup sweep takes its rank-64 updates on the tensor cores
+    (tcgen05): superblock counts 2–4, remainders of 0, 16, 32 and 48 pivots for the CUDA-core
+    blocks, λ blocks of 0, 37, 90 (not multiples of 4), 200 and 201 rows (two λ tiles), a
+    Schur complement past the register-tile Cholesky (nineq > 176), against the oracle."""
+    from paper_1703_00443_gb300 import default_options
+    from paper_1703_00443_gb300.qp import uses_tensor_cores
+    opts = default_options(torch.float32)
+    opts.path = path
+    assert uses_tensor_cores(torch.float32, n, nineq, neq, options=opts)
+    B = 3
+    batch = inputs.random_batch(B, n, nineq, neq, workload=inputs.WL_PLAIN, dtype=np.float32,
+                                start=6000)
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PLAIN, start=6000)
+    out = _run_opts(batch, g, np.float32, opts)
+    assert (out["status"] == 0).all(), out["status"]
+    _compare(batch, g, out, range(B), 1e-5, 1e-4, ltol=1e-4)

@@ -23,6 +23,23 @@ def _pool(sizes, seed=3):
 
 
 def _alone(data, g):
+    """The request solved alone: by qp_forward/qp_backward, or, for sizes whose fixed-size
+    setup sweep takes the tensor cores (the server's packed kernels sweep on CUDA cores), as a
+    packed batch of one."""
+    from paper_1703_00443_gb300.packed import PackedBatch
+    from paper_1703_00443_gb300.qp import uses_tensor_cores
+    n, p, m = data[0].shape[0], data[2].shape[0], data[4].shape[0]
+    if uses_tensor_cores(torch.float32, n, p, m):
+        pb = PackedBatch([(n, p, m)], device=DEV)
+        P = pb.pack([data])
+        fo = pb.forward(*P)
+        go = pb.backward(P[0], P[2], P[4], pb.pack_vec([g], "q"))
+        torch.cuda.synchronize()
+        out = {"z": pb.unpack(fo.z, "q")[0], "lam": pb.unpack(fo.lam, "h")[0],
+               "nu": pb.unpack(fo.nu, "b")[0]}
+        for k, key, t in zip(NAMES, pb.KEYS, go):
+            out[k] = pb.unpack(t, key)[0]
+        return {k: v.cpu().numpy() for k, v in out.items()}
     T = [torch.from_numpy(x).unsqueeze(0).to(DEV) for x in data]
     f = qp_forward(*T)
     gr = qp_backward(f, torch.from_numpy(g).unsqueeze(0).to(DEV))
