@@ -268,7 +268,7 @@ def serving_run(dev, rates, count):
     try:
         # warm-up at the highest offered rate, so batches reach their steady-state sizes and
         # the server's pinned staging buffers their final size before anything is timed
-        poisson_run(server, pool, max(rates), min(400, count), seed=99)
+        poisson_run(server, pool, max(rates), min(1000, count), seed=99)
         for k, rate in enumerate(rates):
             server.latencies.clear()
             server.batch_sizes.clear()
@@ -287,8 +287,37 @@ def serving_run(dev, rates, count):
                                                   retire=st["host_retire_ms_per_batch"])})
     finally:
         server.close()
-    return {"runs": runs, "max_inflight": 4,
+    return {"runs": runs, "max_inflight": 4, "requests_per_rate": count,
+            "batched_same_mix": batched_same_mix(dev, pool, 512),
             "workload": "n log-uniform [16,512], nineq=n, neq=n/4, fwd+bwd, host arrays in/out"}
+
+
+def batched_same_mix(dev, pool, count, steps=3):
+    """The plain batched path on the serving stream's request mix: `count` requests (the pool
+    cycled) known up front, solved as one packed batch with inputs resident on the device;
+    fwd+bwd requests per second, the ceiling the served rates are compared with."""
+    import torch
+    from paper_1703_00443_gb300.packed import PackedBatch
+    reqs = [pool[k % len(pool)] for k in range(count)]
+    sizes = [(d[0].shape[0], d[2].shape[0], d[4].shape[0]) for d, _ in reqs]
+    pb = PackedBatch(sizes, device=dev)
+    P = pb.pack([d for d, _ in reqs])
+    G1 = pb.pack_vec([g for _, g in reqs], "q")
+    fo = pb.forward(*P)
+    go = pb.backward(P[0], P[2], P[4], G1)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pb.forward(*P, out=fo)
+        pb.backward(P[0], P[2], P[4], G1, out=go)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    tm = statistics.mean(ms)
+    return {"requests": count, "ms": tm, "throughput_req_s": count / (tm / 1e3),
+            "note": "one packed batch, inputs resident on the device, no host copies"}
 
 
 def run_reference(args):
@@ -659,9 +688,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the packed and serving runs")
-    ap.add_argument("--serve-rate", default="1000,3000,10000",
+    ap.add_argument("--serve-rate", default="1000,3000,10000,30000,100000",
                     help="offered request rates (req/s), comma-separated")
-    ap.add_argument("--serve-count", type=int, default=1000)
+    ap.add_argument("--serve-count", type=int, default=5000)
     ap.add_argument("--workload", default="headline", choices=["headline", "sweep", "onehot", "uneven"])
     ap.add_argument("--uneven-count", type=int, default=4096)
     ap.add_argument("--sweep-sizes", default="",

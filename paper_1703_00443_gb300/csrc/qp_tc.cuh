@@ -9,8 +9,9 @@
 // pivot (the same sum the 16-pivot blocks of gsweep_setup apply on CUDA cores).  That
 // product is the dense contraction of the setup, and here it runs on the tensor cores:
 //
-//  * phase A (warp 0): the 64 × 64 pivot block is swept in shared memory, pivot after
-//    pivot, recording each pivot's row of multipliers r_k (r_kk = 1/d_k, r_kq = a_kq/d_k);
+//  * phase A: the 64 × 64 pivot block is swept pivot after pivot, in registers (eight
+//    entries per thread; each pivot's row and column go through shared memory), recording
+//    each pivot's row of multipliers r_k (r_kk = 1/d_k, r_kq = a_kq/d_k);
 //  * phase B (all threads, one row each): every row outside K replays the 64 scalar sweeps
 //    on its 64 entries of K's columns (so the result equals the pivot-by-pivot sweep), and
 //    writes p_iq and c_iq, split into TF32 high and low parts, to the panel tiles in the
@@ -18,10 +19,12 @@
 //  * phase C: for each 128 × 128 output tile, all threads stage the four 32 KB operand tiles
 //    in shared memory (16-byte loads of the contiguous panel tiles, then a proxy fence), one
 //    thread issues 8 K-steps × 3 tcgen05.mma (kind::tf32:
-//    hi·hi + hi·lo + lo·hi, the 3×TF32 split that keeps FP32 accuracy) into a TMEM
-//    accumulator, and all 16 warps read it back (tcgen05.ld) and subtract it from the
-//    matrix in global memory, skipping K's rows and columns and, in the λ-by-λ block, the
-//    strict lower triangle.
+//    hi·hi + hi·lo + lo·hi, the 3×TF32 split that keeps FP32 accuracy) into one of two TMEM
+//    accumulators, and, while the tensor core computes that tile, all 16 warps read the
+//    previous tile's accumulator back (tcgen05.ld) and subtract it from the matrix in global
+//    memory, skipping K's rows and columns and, in the λ-by-λ block, the strict lower
+//    triangle.  The product is formed transposed (c tile as the MMA's A operand), so a TMEM
+//    lane is an output column and each warp's accesses cover consecutive columns of a row.
 //
 // Panel tiles (workspace): four parts (p-hi, p-lo, c-hi, c-lo), each NT = T1 + T2 tiles of
 // 128 rows × 64 columns (T1 = ⌈m1/128⌉ tiles for rows 0..m1−1, T2 = ⌈p/128⌉ for the λ rows
@@ -73,8 +76,8 @@ __host__ __device__ inline size_t tc_panel_bytes(int m1, int p) {
 __device__ void tc_mbar_init(uint64_t* bar);
 __device__ void tc_mbar_inval(uint64_t* bar);
 __device__ bool tc_try_wait(uint64_t* bar, uint32_t parity);
-__device__ void tc_alloc128(uint32_t* slot);
-__device__ void tc_dealloc128(uint32_t tmem);
+__device__ void tc_alloc256(uint32_t* slot);
+__device__ void tc_dealloc256(uint32_t tmem);
 __device__ void tc_mma_tf32(uint32_t tmem, const void* a, const void* b, uint32_t lbo,
                             uint32_t sbo, uint32_t idesc, bool accumulate);
 __device__ void tc_commit(uint64_t* bar);
@@ -115,13 +118,13 @@ __device__ __forceinline__ bool tc_try_wait(uint64_t* bar, uint32_t parity) {
                "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(tc_smem_u32(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
-// TMEM allocation of the 128 columns of one FP32 128 × 128 accumulator (warp-collective).
-__device__ __forceinline__ void tc_alloc128(uint32_t* slot) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;"
+// TMEM allocation of the 256 columns of two FP32 128 × 128 accumulators (warp-collective).
+__device__ __forceinline__ void tc_alloc256(uint32_t* slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
                :: "r"(tc_smem_u32(slot)) : "memory");
 }
-__device__ __forceinline__ void tc_dealloc128(uint32_t tmem) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem) : "memory");
+__device__ __forceinline__ void tc_dealloc256(uint32_t tmem) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
 }
 __device__ __forceinline__ void tc_mma_tf32(uint32_t tmem, const void* a, const void* b,
                                             uint32_t lbo, uint32_t sbo, uint32_t idesc,
@@ -205,16 +208,15 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     part[u] = reinterpret_cast<unsigned char*>(tcp) + (size_t)u * NT * TC_TILE_BYTES;
-  // shared layout from the first 1024-byte boundary: phase C operands A-hi, A-lo, B-hi, B-lo
-  // at 0 / 32 / 64 / 96 KB, then the mbarrier, the TMEM address and a flag; phases A/B reuse
-  // the operand space
+  // shared layout from the first 1024-byte boundary: phase C operand tiles p-hi, p-lo (sA),
+  // c-hi, c-lo (sBt) at 0 / 32 / 64 / 96 KB, then the mbarrier, the TMEM address and a flag;
+  // phases A/B reuse the operand space
   unsigned char* cb = cb0 + ((1024 - (reinterpret_cast<uintptr_t>(cb0) & 1023)) & 1023);
   unsigned char* sA[2] = {cb, cb + TC_TILE_BYTES};
   unsigned char* sBt[2] = {cb + 2 * TC_TILE_BYTES, cb + 3 * TC_TILE_BYTES};
-  float* sB = reinterpret_cast<float*>(cb);                    // 64 × 64 pivot block
+  float* rowbuf = reinterpret_cast<float*>(cb);               // pivot row, two buffers
+  float* colbuf = rowbuf + 2 * TC_KB;                          // pivot column, two buffers
   float* sR = reinterpret_cast<float*>(cb + 16384);            // 64 × 64 multipliers
-  float* colk = reinterpret_cast<float*>(cb + 4 * TC_TILE_BYTES - 512);   // inside B-lo
-  float* rowk = colk + 64;
   uint64_t* bar_mma = reinterpret_cast<uint64_t*>(cb + 4 * TC_TILE_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(cb + 4 * TC_TILE_BYTES + 16);
   int* flag = reinterpret_cast<int*>(cb + 4 * TC_TILE_BYTES + 20);
@@ -237,7 +239,7 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
     flag[0] = 0;
   }
   __syncwarp();
-  if (warp == 0) tc_alloc128(tslot);
+  if (warp == 0) tc_alloc256(tslot);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -247,45 +249,52 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
 
   for (int sb = 0; sb < nsb && ok; ++sb) {
     const int k0 = sb * TC_KB;
-    // ---- phase A (warp 0): sweep the pivot block, recording the multipliers.
-    if (warp == 0) {
-      for (int e = lane; e < TC_KB * TC_KB; e += 32)
-        sB[e] = SR[(size_t)(k0 + e / TC_KB) * ldS + k0 + e % TC_KB];
-      __syncwarp();
+    // ---- phase A: sweep the pivot block, recording the multipliers.  Thread t holds the
+    // eight entries of column t % 64 in rows t / 64 + 8u in registers; per pivot, the owners
+    // of its row and column publish them (double-buffered by pivot parity, one barrier per
+    // pivot) and every thread updates its entries.
+    {
+      const int pc = tid & (TC_KB - 1), pr0 = tid >> 6;
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = SR[(size_t)(k0 + pr0 + 8 * u) * ldS + k0 + pc];
       bool good = true;
       for (int k = 0; k < TC_KB; ++k) {
-        const float d = sB[k * TC_KB + k];
-        const int kk = k0 + k;
-        good = good && isfinite(d) && (kk < n ? d > zthr : (kk < nz ? d > 0.f : d < 0.f));
-        const float dinv = 1.f / d;
-        colk[lane] = sB[lane * TC_KB + k];
-        colk[lane + 32] = sB[(lane + 32) * TC_KB + k];
-        rowk[lane] = sB[k * TC_KB + lane];
-        rowk[lane + 32] = sB[k * TC_KB + lane + 32];
-        sR[k * TC_KB + lane] = (lane == k) ? dinv : sB[k * TC_KB + lane] * dinv;
-        sR[k * TC_KB + lane + 32] = (lane + 32 == k) ? dinv : sB[k * TC_KB + lane + 32] * dinv;
-        __syncwarp();
-#pragma unroll 4
-        for (int r = 0; r < TC_KB; ++r) {
-          const float f = colk[r] * dinv;
+        float* rowb = rowbuf + (k & 1) * TC_KB;
+        float* colb = colbuf + (k & 1) * TC_KB;
+        const bool rowown = pr0 == (k & 7);
+        float rk_own = 0.f;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            float v = sB[r * TC_KB + c];
-            if (r != k && c != k) v = fmaf(-f, rowk[c], v);
-            else if (r == k && c == k) v = -dinv;
-            else v = v * dinv;
-            sB[r * TC_KB + c] = v;
-          }
+        for (int u = 0; u < 8; ++u)
+          if (rowown && u == (k >> 3)) rk_own = v[u];
+        if (rowown) rowb[pc] = rk_own;
+        if (pc == k) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) colb[pr0 + 8 * u] = v[u];
         }
-        __syncwarp();
+        __syncthreads();
+        const float d = rowb[k];
+        const float dinv = 1.f / d;
+        if (tid == 0) {
+          const int kk = k0 + k;
+          good = good && isfinite(d) && (kk < n ? d > zthr : (kk < nz ? d > 0.f : d < 0.f));
+        }
+        const float rk = rowb[pc];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r = pr0 + 8 * u;
+          if (r != k && pc != k) v[u] = fmaf(-(colb[r] * dinv), rk, v[u]);
+          else if (r == k && pc == k) v[u] = -dinv;
+          else v[u] = v[u] * dinv;
+        }
+        if (rowown) sR[k * TC_KB + pc] = (pc == k) ? dinv : rk * dinv;
       }
-      for (int e = lane; e < TC_KB * TC_KB; e += 32)
-        SR[(size_t)(k0 + e / TC_KB) * ldS + k0 + e % TC_KB] = sB[e];
-      if (lane == 0) flag[0] = good ? 0 : 1;
+      if (tid == 0) flag[0] = good ? 0 : 1;
+      __syncthreads();
+      if (flag[0]) { ok = false; break; }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) SR[(size_t)(k0 + pr0 + 8 * u) * ldS + k0 + pc] = v[u];
     }
-    __syncthreads();
-    if (flag[0]) { ok = false; break; }
     // ---- phase B: replay the 64 sweeps on every row outside the superblock; write the
     // panels (p = ĉ/d and c = ĉ, TF32 hi and lo) and the row's superblock entries.
     for (int i = tid; i < N; i += NTHREADS) {
@@ -345,11 +354,10 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
     __syncthreads();
     // ---- phase C: the rank-64 update, one 128 × 128 output tile at a time.  SR tiles:
     // row tiles 0..NT−1 (both segments) × column tiles 0..T1−1; λ-by-λ tiles: row tile I ≤
-    // column tile J among the T2 λ tiles.
-    const int nsr = NT * T1, nll = T2 * (T2 + 1) / 2;
-    int prevA = -1;
-    for (int t = 0; t < nsr + nll && ok; ++t) {
-      int ta, tbi;
+    // column tile J among the T2 λ tiles.  Tile t accumulates in TMEM columns 128·(t & 1);
+    // its epilogue runs while the tensor core computes tile t + 1.
+    const int nsr = NT * T1, nll = T2 * (T2 + 1) / 2, ntiles = nsr + nll;
+    auto tile_of = [&](int t, int& ta, int& tbi) {
       if (t < nsr) {
         ta = t / T1; tbi = t - ta * T1;
       } else {
@@ -357,82 +365,106 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
         while (u >= T2 - I) { u -= T2 - I; ++I; }
         ta = T1 + I; tbi = T1 + I + u;
       }
-      // stage the operand tiles (A only when the row tile changes); the MMA of the previous
-      // tile has completed, so its operands may be overwritten
-      {
-        const bool newA = ta != prevA;
-        const float4* src[4] = {
-            reinterpret_cast<const float4*>(part[0] + (size_t)ta * TC_TILE_BYTES),
-            reinterpret_cast<const float4*>(part[1] + (size_t)ta * TC_TILE_BYTES),
-            reinterpret_cast<const float4*>(part[2] + (size_t)tbi * TC_TILE_BYTES),
-            reinterpret_cast<const float4*>(part[3] + (size_t)tbi * TC_TILE_BYTES)};
-        float4* dst[4] = {reinterpret_cast<float4*>(sA[0]), reinterpret_cast<float4*>(sA[1]),
-                          reinterpret_cast<float4*>(sBt[0]), reinterpret_cast<float4*>(sBt[1])};
-        constexpr int NV = (int)(TC_TILE_BYTES / 16);
-        for (int u = newA ? 0 : 2; u < 4; ++u)
-          for (int e = tid; e < NV; e += NTHREADS) dst[u][e] = src[u][e];
-        prevA = ta;
-      }
-      tc_proxy_fence();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        constexpr uint32_t id = tc_idesc(TC_TM, TC_TN);
+    };
+    int prevA = -1, pta = 0, ptb = 0;
+    for (int t = 0; t <= ntiles && ok; ++t) {
+      int ta = 0, tbi = 0;
+      if (t < ntiles) {
+        tile_of(t, ta, tbi);
+        // stage the operand tiles (A only when the row tile changes); the MMA of tile t − 1
+        // has completed, so its operands may be overwritten.  All loads first, then stores.
+        constexpr int PER = (int)(TC_TILE_BYTES / 16) / NTHREADS;   // float4 per thread, part
+        // h = 0: the row tile's p panel (kept while the row tile stays), h = 1: the column
+        // tile's c panel (every tile); hi and lo parts each
+        for (int h = (ta != prevA) ? 0 : 1; h < 2; ++h) {
+          const int tt = h ? tbi : ta;
+          const float4* __restrict__ s0 =
+              reinterpret_cast<const float4*>(part[2 * h] + (size_t)tt * TC_TILE_BYTES);
+          const float4* __restrict__ s1 =
+              reinterpret_cast<const float4*>(part[2 * h + 1] + (size_t)tt * TC_TILE_BYTES);
+          float4 r[2 * PER];
 #pragma unroll
-        for (int s = 0; s < TC_KB / 8; ++s) {
-          const uint32_t ko = (uint32_t)s * 256;   // two K-adjacent core matrices per step
-          tc_mma_tf32(tmem, sA[0] + ko, sBt[0] + ko, 128, 2048, id, s > 0);   // hi · hi
-          tc_mma_tf32(tmem, sA[0] + ko, sBt[1] + ko, 128, 2048, id, true);    // hi · lo
-          tc_mma_tf32(tmem, sA[1] + ko, sBt[0] + ko, 128, 2048, id, true);    // lo · hi
+          for (int j = 0; j < PER; ++j) {
+            r[j] = s0[tid + j * NTHREADS];
+            r[PER + j] = s1[tid + j * NTHREADS];
+          }
+          float4* d0 = reinterpret_cast<float4*>(h ? sBt[0] : sA[0]);
+          float4* d1 = reinterpret_cast<float4*>(h ? sBt[1] : sA[1]);
+#pragma unroll
+          for (int j = 0; j < PER; ++j) {
+            d0[tid + j * NTHREADS] = r[j];
+            d1[tid + j * NTHREADS] = r[PER + j];
+          }
         }
-        // arrives on bar_mma once every MMA issued so far has completed
-        tc_commit(bar_mma);
+        prevA = ta;
+        tc_proxy_fence();
+        __syncthreads();
+        if (tid == 0) {
+          // D = C_tile · P_tileᵀ: TMEM lane l is the output column of c-panel row l and TMEM
+          // column c the output row of p-panel row c, so the epilogue's warps touch
+          // consecutive columns of one row per access
+          tc_fence_after();
+          constexpr uint32_t id = tc_idesc(TC_TM, TC_TN);
+          const uint32_t acc = tmem + (uint32_t)(TC_TN * (t & 1));
+#pragma unroll
+          for (int s = 0; s < TC_KB / 8; ++s) {
+            const uint32_t ko = (uint32_t)s * 256;   // two K-adjacent core matrices per step
+            tc_mma_tf32(acc, sBt[0] + ko, sA[0] + ko, 128, 2048, id, s > 0);   // hi · hi
+            tc_mma_tf32(acc, sBt[0] + ko, sA[1] + ko, 128, 2048, id, true);    // hi · lo
+            tc_mma_tf32(acc, sBt[1] + ko, sA[0] + ko, 128, 2048, id, true);    // lo · hi
+          }
+          // arrives on bar_mma once every MMA issued so far has completed
+          tc_commit(bar_mma);
+        }
       }
-      const bool done = tc_wait(bar_mma, ph_mma);
-      ph_mma ^= 1;
-      if (!done) atomicExch(flag, 2);
-      __syncwarp();
-      tc_fence_after();
-      // epilogue: warp w reads TMEM lanes 32·(w%4)… (tile rows) and columns 32·(w/4)…
-      {
+      if (t > 0) {
+        // epilogue of tile t − 1 (its MMA completed before the last barrier): warp w reads
+        // TMEM lanes 32·(w%4)… (tile columns) and TMEM columns 32·(w/4)… (tile rows); lane
+        // l holds column 32·(w%4) + l of 32 consecutive rows
+        __syncwarp();
+        tc_fence_after();
         const int qd = warp & 3, cg = warp >> 2;
         float d[32];
-        tc_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * cg), d);
-        const int lr = 32 * qd + lane;                   // row within the tile
-        const int lc = 32 * cg;                          // first column within the tile
-        if (done) {
-          if (t < nsr) {
-            const int gi = ta < T1 ? ta * TC_TM + lr : m1 + (ta - T1) * TC_TM + lr;
-            const int gj = tbi * TC_TM + lc;
-            const bool rowok = (ta < T1 ? gi < m1 : gi < N) && !(gi >= k0 && gi < k0 + TC_KB);
-            const bool colok = gj < m1 && !(gj >= k0 && gj < k0 + TC_KB);
-            if (rowok && colok) {
-              float* c = SR + (size_t)gi * ldS + gj;
+        tc_ld32(tmem + (uint32_t)(TC_TN * ((t - 1) & 1)) + ((uint32_t)(32 * qd) << 16) +
+                    (uint32_t)(32 * cg), d);
+        const int lc = 32 * qd + lane;                   // column within the tile
+        const int lr = 32 * cg;                          // first row within the tile
+        if (t - 1 < nsr) {
+          const int j = ptb * TC_TM + lc;
+          const bool colok = j < m1 && !(j >= k0 && j < k0 + TC_KB);
+          const int ib = pta < T1 ? pta * TC_TM + lr : m1 + (pta - T1) * TC_TM + lr;
+          const int iend = pta < T1 ? m1 : N;
+          float* c = SR + (size_t)ib * ldS + j;
+          float x[32];
 #pragma unroll
-              for (int q = 0; q < 32; q += 4) {
-                if (gj + q < m1) {
-                  float4 x = *reinterpret_cast<float4*>(c + q);
-                  x.x -= d[q]; x.y -= d[q + 1]; x.z -= d[q + 2]; x.w -= d[q + 3];
-                  *reinterpret_cast<float4*>(c + q) = x;
-                }
-              }
-            }
-          } else {
-            const int a = (ta - T1) * TC_TM + lr;
-            const int b0 = (tbi - T1) * TC_TM + lc;
-            if (a < p) {
-#pragma unroll 4
-              for (int q = 0; q < 32; ++q) {
-                const int b = b0 + q;
-                if (b < p && b >= a) {
-                  if (b == a) dM[a] -= d[q];
-                  else Mb[(size_t)a * ldM + b] -= d[q];
-                }
-              }
+          for (int r = 0; r < 32; ++r) {
+            const int i = ib + r;
+            if (colok && i < iend && !(i >= k0 && i < k0 + TC_KB)) x[r] = c[(size_t)r * ldS];
+          }
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            const int i = ib + r;
+            if (colok && i < iend && !(i >= k0 && i < k0 + TC_KB)) c[(size_t)r * ldS] = x[r] - d[r];
+          }
+        } else {
+          const int b = (ptb - T1) * TC_TM + lc;
+          const int ab = (pta - T1) * TC_TM + lr;
+#pragma unroll 8
+          for (int r = 0; r < 32; ++r) {
+            const int a = ab + r;
+            if (a < p && b < p && b >= a) {
+              if (b == a) dM[a] -= d[r];
+              else Mb[(size_t)a * ldM + b] -= d[r];
             }
           }
         }
       }
+      if (t < ntiles) {
+        if (!tc_wait(bar_mma, ph_mma)) atomicExch(flag, 2);
+        ph_mma ^= 1;
+        pta = ta; ptb = tbi;
+      }
+      // the epilogue's TMEM reads finish before the next MMA reuses its accumulator
       tc_fence_before();
       __syncthreads();
       if (flag[0]) ok = false;
@@ -446,7 +478,7 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
   if (warp == 0) {
     __syncwarp();
     tc_fence_after();
-    tc_dealloc128(tmem);
+    tc_dealloc256(tmem);
   }
   if (tid == 0) {
     tc_mbar_inval(bar_mma);

@@ -40,8 +40,8 @@ inline bool tc_try_wait(uint64_t* bar, uint32_t parity) {
   return done;
 }
 // alloc and dealloc are warp-collective: lane 0 of the calling warp acts for it
-inline void tc_alloc128(uint32_t* slot) {
-  const uint32_t ncols = 128;
+inline void tc_alloc256(uint32_t* slot) {
+  const uint32_t ncols = 256;
   if (threadIdx.x & 31) return;
   EmuTmem& t = emu_tmem();
   if (ncols < 32 || ncols > 512 || (ncols & (ncols - 1))) emu_tc_fail("bad column count");
@@ -51,8 +51,8 @@ inline void tc_alloc128(uint32_t* slot) {
     for (float& x : row) x = std::nanf("");
   *slot = 0;
 }
-inline void tc_dealloc128(uint32_t tmem) {
-  const uint32_t ncols = 128;
+inline void tc_dealloc256(uint32_t tmem) {
+  const uint32_t ncols = 256;
   if (threadIdx.x & 31) return;
   EmuTmem& t = emu_tmem();
   if (tmem != 0 || (int)ncols != t.cols) emu_tc_fail("dealloc does not match alloc");
