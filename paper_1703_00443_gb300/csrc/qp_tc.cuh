@@ -434,28 +434,49 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
           const bool colok = j < m1 && !(j >= k0 && j < k0 + TC_KB);
           const int ib = pta < T1 ? pta * TC_TM + lr : m1 + (pta - T1) * TC_TM + lr;
           const int iend = pta < T1 ? m1 : N;
-          float* c = SR + (size_t)ib * ldS + j;
-          float x[32];
+          float* __restrict__ c = SR + (size_t)ib * ldS + j;
+          // all 32 loads in flight before the first store
+          uint32_t live = 0;
 #pragma unroll
           for (int r = 0; r < 32; ++r) {
             const int i = ib + r;
-            if (colok && i < iend && !(i >= k0 && i < k0 + TC_KB)) x[r] = c[(size_t)r * ldS];
+            if (colok && i < iend && !(i >= k0 && i < k0 + TC_KB)) live |= 1u << r;
           }
 #pragma unroll
-          for (int r = 0; r < 32; ++r) {
-            const int i = ib + r;
-            if (colok && i < iend && !(i >= k0 && i < k0 + TC_KB)) c[(size_t)r * ldS] = x[r] - d[r];
+          for (int hh = 0; hh < 32; hh += 16) {   // 16 loads in flight, then 16 stores
+            float x[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+              if (live >> (hh + r) & 1) x[r] = c[(size_t)(hh + r) * ldS];
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+              if (live >> (hh + r) & 1) c[(size_t)(hh + r) * ldS] = x[r] - d[hh + r];
           }
         } else {
+          // λ-by-λ block: the strict upper triangle in Mb, the diagonal in dM; loads first
           const int b = (ptb - T1) * TC_TM + lc;
           const int ab = (pta - T1) * TC_TM + lr;
-#pragma unroll 8
+          float* __restrict__ mrow = Mb + (size_t)ab * ldM + b;
+          uint32_t live = 0;
+#pragma unroll
           for (int r = 0; r < 32; ++r) {
             const int a = ab + r;
-            if (a < p && b < p && b >= a) {
-              if (b == a) dM[a] -= d[r];
-              else Mb[(size_t)a * ldM + b] -= d[r];
-            }
+            if (a < p && b < p && b >= a) live |= 1u << r;
+          }
+          const int rdiag = b - ab;   // the row whose entry is the diagonal (if 0 ≤ rdiag < 32)
+#pragma unroll
+          for (int hh = 0; hh < 32; hh += 16) {
+            float x[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+              if (live >> (hh + r) & 1)
+                x[r] = (hh + r == rdiag) ? dM[ab + hh + r] : mrow[(size_t)(hh + r) * ldM];
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+              if (live >> (hh + r) & 1) {
+                if (hh + r == rdiag) dM[ab + hh + r] = x[r] - d[hh + r];
+                else mrow[(size_t)(hh + r) * ldM] = x[r] - d[hh + r];
+              }
           }
         }
       }
