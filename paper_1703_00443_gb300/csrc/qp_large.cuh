@@ -58,14 +58,14 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
   int kstart = 0;
 #if defined(__CUDA_ARCH__) || defined(QP_HOST_EMULATION)
   if constexpr (sizeof(T) == 4) {
-    // FP32 with the workspace's panel tiles: whole 64-pivot superblocks on the tensor cores,
-    // the remaining 16-pivot blocks below.
+    // FP32 with the workspace's panel tiles: every pivot in 64-pivot superblocks on the
+    // tensor cores (the last one partial), none left for the 16-pivot blocks below.
     if (tcp != nullptr) {
-      const int nsb = m1 / TC_KB;
+      const int nsb = (m1 + TC_KB - 1) / TC_KB;
       if (!tc_sweep_superblocks(n, nz, p, m, nsb, SR, Mb, ldM, dM, tcp,
                                 reinterpret_cast<unsigned char*>(sm), zthr))
         return false;
-      kstart = nsb * TC_KB;
+      kstart = m1;
     }
   }
 #endif

@@ -192,7 +192,8 @@ __device__ __forceinline__ float tc_hi(float x) {
   return r;
 }
 
-// Superblock sweeps of pivots [0, 64·nsb) of the matrix gsweep_setup holds (SR: rows 0..N−1
+// Superblock sweeps of pivots [0, m1) in nsb = ⌈m1/64⌉ superblocks (the last one 16, 32, 48
+// or 64 pivots) of the matrix gsweep_setup holds (SR: rows 0..N−1
 // × columns 0..m1−1, row stride m1; the λ-by-λ block: strict upper triangle of Mb (row stride
 // ldM) plus dM).  `tcp` is the panel-tile region of the workspace, `cb0` the shared work
 // region (≥ TC_SMEM_BYTES, 16-byte aligned).  Pivot sign tests as in gsweep_setup.  Returns
@@ -249,6 +250,8 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
 
   for (int sb = 0; sb < nsb && ok; ++sb) {
     const int k0 = sb * TC_KB;
+    const int kb = m1 - k0 < TC_KB ? m1 - k0 : TC_KB;   // the last superblock may be partial
+    // (kb a multiple of 16: entries outside its kb × kb pivot block are held as zeros)
     // ---- phase A: sweep the pivot block, recording the multipliers.  Thread t holds the
     // eight entries of column t % 64 in rows t / 64 + 8u in registers; per pivot, the owners
     // of its row and column publish them (double-buffered by pivot parity, one barrier per
@@ -257,9 +260,10 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
       const int pc = tid & (TC_KB - 1), pr0 = tid >> 6;
       float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = SR[(size_t)(k0 + pr0 + 8 * u) * ldS + k0 + pc];
+      for (int u = 0; u < 8; ++u)
+        v[u] = (pr0 + 8 * u < kb && pc < kb) ? SR[(size_t)(k0 + pr0 + 8 * u) * ldS + k0 + pc] : 0.f;
       bool good = true;
-      for (int k = 0; k < TC_KB; ++k) {
+      for (int k = 0; k < kb; ++k) {
         float* rowb = rowbuf + (k & 1) * TC_KB;
         float* colb = colbuf + (k & 1) * TC_KB;
         const bool rowown = pr0 == (k & 7);
@@ -293,17 +297,19 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
       __syncthreads();
       if (flag[0]) { ok = false; break; }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) SR[(size_t)(k0 + pr0 + 8 * u) * ldS + k0 + pc] = v[u];
+      for (int u = 0; u < 8; ++u)
+        if (pr0 + 8 * u < kb && pc < kb) SR[(size_t)(k0 + pr0 + 8 * u) * ldS + k0 + pc] = v[u];
     }
     // ---- phase B: replay the 64 sweeps on every row outside the superblock; write the
     // panels (p = ĉ/d and c = ĉ, TF32 hi and lo) and the row's superblock entries.
     for (int i = tid; i < N; i += NTHREADS) {
-      if (i >= k0 && i < k0 + TC_KB) continue;
+      if (i >= k0 && i < k0 + kb) continue;
       float* row = SR + (size_t)i * ldS + k0;
       float v[TC_KB];
 #pragma unroll
       for (int q = 0; q < TC_KB; q += 4) {
-        const float4 t = *reinterpret_cast<const float4*>(row + q);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < kb) t = *reinterpret_cast<const float4*>(row + q);
         v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
       }
       const int seg1 = i >= m1;
@@ -316,20 +322,23 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int k = 4 * g + u;
-          const float c = v[k];
-          const float4* rk = reinterpret_cast<const float4*>(sR + k * TC_KB);
-          const float dk = sR[k * TC_KB + k];
+          cc[u] = pp[u] = 0.f;   // pivots past kb: zero panel columns
+          if (k < kb) {
+            const float c = v[k];
+            const float4* rk = reinterpret_cast<const float4*>(sR + k * TC_KB);
+            const float dk = sR[k * TC_KB + k];
 #pragma unroll
-          for (int q4 = 0; q4 < TC_KB / 4; ++q4) {
-            const float4 w = rk[q4];
-            v[4 * q4 + 0] = fmaf(-c, w.x, v[4 * q4 + 0]);
-            v[4 * q4 + 1] = fmaf(-c, w.y, v[4 * q4 + 1]);
-            v[4 * q4 + 2] = fmaf(-c, w.z, v[4 * q4 + 2]);
-            v[4 * q4 + 3] = fmaf(-c, w.w, v[4 * q4 + 3]);
+            for (int q4 = 0; q4 < TC_KB / 4; ++q4) {
+              const float4 w = rk[q4];
+              v[4 * q4 + 0] = fmaf(-c, w.x, v[4 * q4 + 0]);
+              v[4 * q4 + 1] = fmaf(-c, w.y, v[4 * q4 + 1]);
+              v[4 * q4 + 2] = fmaf(-c, w.z, v[4 * q4 + 2]);
+              v[4 * q4 + 3] = fmaf(-c, w.w, v[4 * q4 + 3]);
+            }
+            v[k] = c * dk;   // overwrite the pivot column's (meaningless) update
+            cc[u] = c;
+            pp[u] = c * dk;
           }
-          v[k] = c * dk;   // overwrite the pivot column's (meaningless) update
-          cc[u] = c;
-          pp[u] = c * dk;
         }
         const uint32_t o = tc_off(r, 4 * g);
         float ph[4], pl[4], ch[4], cl[4];
@@ -345,10 +354,11 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
       }
 #pragma unroll
       for (int q = 0; q < TC_KB; q += 4)
-        *reinterpret_cast<float4*>(row + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        if (q < kb) *reinterpret_cast<float4*>(row + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
       if (i < m1) {
 #pragma unroll
-        for (int q = 0; q < TC_KB; ++q) SR[(size_t)(k0 + q) * ldS + i] = v[q];
+        for (int q = 0; q < TC_KB; ++q)
+          if (q < kb) SR[(size_t)(k0 + q) * ldS + i] = v[q];
       }
     }
     __syncthreads();
@@ -431,7 +441,7 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
         const int lr = 32 * cg;                          // first row within the tile
         if (t - 1 < nsr) {
           const int j = ptb * TC_TM + lc;
-          const bool colok = j < m1 && !(j >= k0 && j < k0 + TC_KB);
+          const bool colok = j < m1 && !(j >= k0 && j < k0 + kb);
           const int ib = pta < T1 ? pta * TC_TM + lr : m1 + (pta - T1) * TC_TM + lr;
           const int iend = pta < T1 ? m1 : N;
           float* __restrict__ c = SR + (size_t)ib * ldS + j;
@@ -440,7 +450,7 @@ static __device__ __noinline__ bool tc_sweep_superblocks(int n, int nz, int p, i
 #pragma unroll
           for (int r = 0; r < 32; ++r) {
             const int i = ib + r;
-            if (colok && i < iend && !(i >= k0 && i < k0 + TC_KB)) live |= 1u << r;
+            if (colok && i < iend && !(i >= k0 && i < k0 + kb)) live |= 1u << r;
           }
 #pragma unroll
           for (int hh = 0; hh < 32; hh += 16) {   // 16 loads in flight, then 16 stores

@@ -304,8 +304,8 @@ def test_global_memory_kernel_large_sizes(n, nineq, neq):
                                               (200, 201, 17, 0)])
 def test_tensor_core_setup_sweep(n, nineq, neq, path):
     """FP32 sizes whose fixed-size setup sweep takes its rank-64 updates on the tensor cores
-    (tcgen05): superblock counts 2–4, remainders of 0, 16, 32 and 48 pivots for the CUDA-core
-    blocks, λ blocks of 0, 37, 90 (not multiples of 4), 200 and 201 rows (two λ tiles), a
+    (tcgen05): 2–4 superblocks, the last one partial with 16, 32 or 48 pivots or whole,
+    λ blocks of 0, 37, 90 (not multiples of 4), 200 and 201 rows (two λ tiles), a
     Schur complement past the register-tile Cholesky (nineq > 176), against the oracle."""
     from paper_1703_00443_gb300 import default_options
     from paper_1703_00443_gb300.qp import uses_tensor_cores

@@ -95,7 +95,7 @@ def _run(exe, B, n, p, m, dtype, path, start):
 @pytest.mark.parametrize("B,n,p,m,dtype,path,ztol,gtol", [
     (2, 20, 30, 5, np.float32, 0, 1e-5, 1e-4),      # shared-memory path, FP32
     (1, 24, 40, 4, np.float64, 1, 1e-9, 1e-8),      # global-memory path forced, FP64
-    (1, 100, 60, 44, np.float32, 1, 1e-5, 1e-4),    # tensor-core setup sweep, 16-pivot tail
+    (1, 100, 60, 44, np.float32, 1, 1e-5, 1e-4),    # tensor-core setup sweep, 16-pivot last superblock
     (1, 140, 200, 30, np.float32, 0, 1e-5, 1e-4),   # global path by size, two λ tiles
 ])
 def test_emulated_kernels_are_memory_safe_and_match_the_oracle(driver, B, n, p, m, dtype, path,
