@@ -251,7 +251,11 @@ def cpu_baseline(n, p, m, budget_s=15.0, gpu_out=None):
     return res, acc
 
 
-def serving_run(dev, rates, count):
+def _classes(args):
+    return tuple(int(v) for v in str(args.serve_classes).split(",") if v)
+
+
+def serving_run(dev, rates, count, inflight=4, classes=(192,), max_batch=512):
     """Poisson streams of fwd+bwd requests (n log-uniform in [16, 512], nineq = n, neq = n/4)
     through the continuous-batching server, one run per offered rate; p50/p99 latency from
     arrival to result, throughput, and the scheduler's host time per batch."""
@@ -263,7 +267,8 @@ def serving_run(dev, rates, count):
         data = inputs.random_qp(nn, pp, mm, workload=inputs.WL_SERVE, index=i)
         gg = inputs.upstream_grad(1, nn, workload=inputs.WL_SERVE, start=i)[0]
         pool.append((tuple(np.float32(x) for x in data), np.float32(gg)))
-    server = QPServer(device=dev, max_inflight=4, max_batch=512)
+    server = QPServer(device=dev, max_inflight=inflight, max_batch=max_batch,
+                      size_classes=tuple(classes))
     runs = []
     try:
         # warm-up at the highest offered rate, so batches reach their steady-state sizes and
@@ -287,7 +292,8 @@ def serving_run(dev, rates, count):
                                                   retire=st["host_retire_ms_per_batch"])})
     finally:
         server.close()
-    return {"runs": runs, "max_inflight": 4, "requests_per_rate": count,
+    return {"runs": runs, "max_inflight": inflight, "size_classes": list(classes),
+            "max_batch": max_batch, "requests_per_rate": count,
             "batched_same_mix": batched_same_mix(dev, pool, 512),
             "workload": "n log-uniform [16,512], nineq=n, neq=n/4, fwd+bwd, host arrays in/out"}
 
@@ -518,7 +524,8 @@ def run_gpu(args):
     served = None
     if not args.no_extras and ws == 1:
         served = serving_run(dev, [float(r) for r in str(args.serve_rate).split(",")],
-                             args.serve_count)
+                             args.serve_count, args.serve_inflight, _classes(args),
+                             args.serve_max_batch)
     cpu, acc = (None, None)
     if not args.no_cpu_baseline and ws == 1:
         cpu, acc = cpu_baseline(n, p, m, budget_s=args.cpu_budget, gpu_out=gpu_out)
@@ -672,6 +679,12 @@ def run_workload(args):
         line.update({"metric": "structured one-hot QP fwd+bwd solves/sec (n=64, neq=40, z>=0, batch 512)",
                      "value": B / (ms / 1e3), "ms_per_step": ms,
                      "iters_mean": float(f.iters.float().mean()), "converged": int((f.status == 0).sum())})
+    elif args.workload == "serving":
+        line.update({"metric": "served fwd+bwd requests/sec and p50/p99 latency (Poisson arrivals)",
+                     "unit": "req/s"})
+        line.update(serving_run(dev, [float(r) for r in str(args.serve_rate).split(",")],
+                                args.serve_count, args.serve_inflight, _classes(args),
+                                args.serve_max_batch))
     elif args.workload == "uneven":
         line.update({"metric": "uneven batch fwd+bwd solves/sec (two persistent kernels forward, one backward)"})
         line.update(uneven_run(dev, args.uneven_count, args.uneven_steps, args.tuned, flush, stream))
@@ -691,7 +704,11 @@ def main():
     ap.add_argument("--serve-rate", default="1000,3000,10000,30000,100000",
                     help="offered request rates (req/s), comma-separated")
     ap.add_argument("--serve-count", type=int, default=5000)
-    ap.add_argument("--workload", default="headline", choices=["headline", "sweep", "onehot", "uneven"])
+    ap.add_argument("--serve-inflight", type=int, default=16, help="server stream slots")
+    ap.add_argument("--serve-classes", default="64,160,320", help="size-class thresholds on n")
+    ap.add_argument("--serve-max-batch", type=int, default=256)
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "sweep", "onehot", "uneven", "serving"])
     ap.add_argument("--uneven-count", type=int, default=4096)
     ap.add_argument("--sweep-sizes", default="",
                     help="sweep points n:batch, comma-separated (default: the full grid)")
