@@ -301,11 +301,12 @@ def test_global_memory_kernel_large_sizes(n, nineq, neq):
 @pytest.mark.parametrize("n,nineq,neq,path", [(100, 60, 44, 1), (100, 100, 50, 1), (96, 37, 32, 1),
                                               (140, 200, 30, 0), (150, 90, 37, 0),
                                               (180, 70, 60, 1), (150, 0, 40, 1),
-                                              (200, 201, 17, 0)])
+                                              (160, 100, 0, 1), (200, 201, 17, 0)])
 def test_tensor_core_setup_sweep(n, nineq, neq, path):
     """FP32 sizes whose fixed-size setup sweep takes its rank-64 updates on the tensor cores
     (tcgen05): 2–4 superblocks, the last one partial with 16, 32 or 48 pivots or whole,
-    λ blocks of 0, 37, 90 (not multiples of 4), 200 and 201 rows (two λ tiles), a
+    λ blocks of 0, 37, 90 (not multiples of 4), 200 and 201 rows (two λ tiles), no equality
+    constraints, a
     Schur complement past the register-tile Cholesky (nineq > 176), against the oracle."""
     from paper_1703_00443_gb300 import default_options
     from paper_1703_00443_gb300.qp import uses_tensor_cores

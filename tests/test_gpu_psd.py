@@ -86,3 +86,18 @@ def test_positive_definite_q_is_not_regularised():
     qp_backward(fwd, torch.ones((4, 20), device=DEV), status=st)
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == 0).all()
+
+
+@pytest.mark.parametrize("rank", [0, 20])
+def test_psd_q_with_tensor_core_setup_fp32(rank):
+    """A linear program and a rank-deficient Q at a size whose setup sweep takes the tensor
+    cores (n = 130, 300 inequalities, 10 equalities): the Q + δI retry of the setup runs the
+    tensor-core superblocks a second time in the same block."""
+    from paper_1703_00443_gb300.qp import uses_tensor_cores
+    n, extra, m = 130, 40, 10
+    assert uses_tensor_cores(torch.float32, n, 2 * n + extra, m)
+    B = 2
+    batch = _batch([inputs.psd_qp(n, extra, m, rank, index=80 + i) for i in range(B)])
+    g = inputs.upstream_grad(B, n, workload=inputs.WL_PSD, start=80)
+    bst = _run_and_compare(batch, g, np.float32, 1e-5, 1e-4, 1e-4)
+    assert ((bst & 0xff) == 0).all() and (bst & FLAG_REGULARIZED_Q).all()
