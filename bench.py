@@ -87,6 +87,30 @@ def profiled_traffic(summary="qp_fwd_kernel_n100_b128.md"):
         return None
 
 
+def measured_hbm_gbs():
+    """The driver's measured copy bandwidth (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def bwd_roofline(n, p, m, B, bwd_ms, esz=4):
+    """HBM roofline of the backward kernel: algorithmic bytes per solve = ∂ℓ/∂z* in and the six
+    gradients out (the workspace the forward left, S/RE and the factor, is read as well and
+    reported beside it)."""
+    alg = esz * n + esz * (n * n + n * p + n * m + n + p + m)
+    m1 = n + (4 - (n + m) % 4) % 4 + m   # n padded to make n + neq a multiple of 4, plus neq
+    ws_read = esz * ((m1 + p) * m1 + p * p)
+    peak, src = measured_hbm_gbs()
+    achieved = alg * B / (bwd_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "qp_bwd_kernel", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": src + " copy bandwidth",
+            "algorithmic_bytes_per_launch": alg * B, "workspace_bytes_read_per_launch": ws_read * B,
+            "traffic": profiled_traffic("qp_bwd_kernel_n100_b128.md")}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -552,6 +576,7 @@ def run_gpu(args):
                      "traffic": profiled_traffic(),
                      "traffic_unit": "bytes per launch (dram read+write, ncu)",
                      "algorithmic_flops_per_launch": f_fwd * B},
+        "roofline_bwd": bwd_roofline(n, p, m, B, step_ms - fwd_mean),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "batched_vs_plain": None if packed_ms is None else {
