@@ -59,8 +59,11 @@ __device__ __noinline__ bool gsweep_setup(int n, int nz, int p, int m, const T* 
 #if defined(__CUDA_ARCH__) || defined(QP_HOST_EMULATION)
   if constexpr (sizeof(T) == 4) {
     // FP32 with the workspace's panel tiles: every pivot in 64-pivot superblocks on the
-    // tensor cores (the last one partial), none left for the 16-pivot blocks below.
-    if (tcp != nullptr) {
+    // tensor cores (the last one partial), none left for the 16-pivot blocks below.  Not for
+    // the regularised retry of a singular Q (delta > 0): its Schur complements are
+    // ill-conditioned by construction, and the backward refinement needs the FP32 sweep's
+    // accuracy there (3×TF32 products carry about 10× the FP32 rounding error).
+    if (tcp != nullptr && delta == T(0)) {
       const int nsb = (m1 + TC_KB - 1) / TC_KB;
       if (!tc_sweep_superblocks(n, nz, p, m, nsb, SR, Mb, ldM, dM, tcp,
                                 reinterpret_cast<unsigned char*>(sm), zthr))

@@ -88,11 +88,12 @@ def test_positive_definite_q_is_not_regularised():
     assert (st.cpu().numpy() == 0).all()
 
 
-@pytest.mark.parametrize("rank", [0, 20])
+@pytest.mark.parametrize("rank", [20, 60])
 def test_psd_q_with_tensor_core_setup_fp32(rank):
-    """A linear program and a rank-deficient Q at a size whose setup sweep takes the tensor
-    cores (n = 130, 300 inequalities, 10 equalities): the Q + δI retry of the setup runs the
-    tensor-core superblocks a second time in the same block."""
+    """Rank-deficient Q at a size whose setup sweep takes the tensor cores (n = 130, 300
+    inequalities, 10 equalities): the first setup, on the tensor cores, meets the singular
+    pivot; the Q + δI retry runs the CUDA-core sweep after the tensor-core superblocks have
+    released their tensor memory in the same block."""
     from paper_1703_00443_gb300.qp import uses_tensor_cores
     n, extra, m = 130, 40, 10
     assert uses_tensor_cores(torch.float32, n, 2 * n + extra, m)
