@@ -172,3 +172,31 @@ def test_backward_rejects_a_forward_of_other_sizes():
     qp_forward(*Ts, workspace=ws)                 # smaller instances written into ws
     grads, bst = _bwd(fb.__class__(**{**fb.__dict__, "workspace": ws}), torch.ones((2, 8), device=DEV))
     assert (bst == STATUS_NO_FORWARD).all()
+
+
+def test_tensor_core_setup_statuses():
+    """At a size whose setup sweep takes the tensor cores: a NaN in Q is caught by the
+    superblock's pivot test (NOT_PD or NUMERICAL, NaN outputs, no hang), a NaN in q by the
+    residual (NUMERICAL), max_iter = 2 returns a finite iterate, and the other instances of
+    the batch converge."""
+    from paper_1703_00443_gb300 import STATUS_NOT_PD
+    from paper_1703_00443_gb300.qp import uses_tensor_cores
+    n, p, m = 140, 200, 30
+    assert uses_tensor_cores(torch.float32, n, p, m)
+    batch = inputs.random_batch(3, n, p, m, workload=inputs.WL_SWEEP, start=90)
+    batch.Q[0, 5, 7] = batch.Q[0, 7, 5] = np.nan
+    batch.q[1, 3] = np.nan
+    fwd = qp_forward(*_dev(batch))
+    grads, bst = _bwd(fwd, torch.ones((3, n), device=DEV))
+    st = fwd.status.cpu().numpy()
+    assert st[0] in (STATUS_NOT_PD, STATUS_NUMERICAL) and st[1] == STATUS_NUMERICAL, st
+    assert st[2] == STATUS_CONVERGED, st
+    assert torch.isnan(fwd.z[0]).all() and torch.isnan(fwd.z[1]).all()
+    assert torch.isfinite(fwd.z[2]).all() and all(torch.isfinite(t[2]).all() for t in grads)
+    opts = default_options(torch.float32)
+    opts.max_iter = 2
+    batch2 = inputs.random_batch(2, n, p, m, workload=inputs.WL_SWEEP, start=95)
+    fwd2 = qp_forward(*_dev(batch2), options=opts)
+    grads2, bst2 = _bwd(fwd2, torch.ones((2, n), device=DEV))
+    assert (fwd2.status.cpu().numpy() == STATUS_MAX_ITER).all()
+    assert torch.isfinite(fwd2.z).all() and all(torch.isfinite(t).all() for t in grads2)
