@@ -43,6 +43,22 @@ def test_host_side_queries():
     assert lib.qp_uses_global_path(0, 500, 500, 250) == 1
     assert lib.qp_supported(0, 500, 500, 250) == 0
     assert lib.qp_supported(0, 256, 512, 64) == 0
+    # the tensor-core setup: FP32 global-path sizes with n + neq ≥ 128 after padding
+    assert lib.qp_uses_tensor_cores(None, 0, 500, 500, 250) == 1
+    assert lib.qp_uses_tensor_cores(None, 0, 100, 100, 50) == 0     # shared-memory kernel
+    assert lib.qp_uses_tensor_cores(None, 1, 500, 500, 250) == 0     # FP64
+    assert lib.qp_uses_tensor_cores(None, 0, 64, 512, 16) == 0       # n + neq < 128
+    assert lib.qp_uses_tensor_cores(None, 7, 500, 500, 250) == -1
+    o = _lib.QPOptions()
+    lib.qp_default_options(0, ctypes.byref(o))
+    o.path = 1
+    assert lib.qp_uses_tensor_cores(ctypes.byref(o), 0, 100, 100, 50) == 1   # forced global
+    # the packed plan leaves out the tensor-core panel tiles (its kernels sweep on CUDA cores)
+    dims = (ctypes.c_int32 * 3)(500, 500, 250)
+    desc = (_lib.QPInstanceDesc * 1)()
+    sz = _lib.QPPackedSizes()
+    assert lib.qp_packed_plan(None, 0, 1, ctypes.cast(dims, ctypes.c_void_p), desc, ctypes.byref(sz)) == 0
+    assert sz.ws_bytes < 256 + lib.qp_workspace_bytes(0, 1, 500, 500, 250)
 
 
 def test_invalid_arguments_rejected_before_launch():
