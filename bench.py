@@ -298,6 +298,7 @@ def serving_run(dev, rates, count, inflight=4, classes=(192,), max_batch=512):
         # warm-up at the highest offered rate, so batches reach their steady-state sizes and
         # the server's pinned staging buffers their final size before anything is timed
         poisson_run(server, pool, max(rates), min(1000, count), seed=99)
+        server.equalize_staging()   # every slot sized for the largest batch seen
         for k, rate in enumerate(rates):
             server.latencies.clear()
             server.batch_sizes.clear()

@@ -185,6 +185,7 @@ class QPServer:
         self.copy_threads = int(copy_threads or min(8, os.cpu_count() or 1))
         esz = 4 if dtype == torch.float32 else 8
         self.staging = [_Staging(dtype, staging_bytes // esz) for _ in range(max_inflight)]
+        self.stage_peak = (0, 0, 0)   # largest batch staging any slot has needed (elements)
         self.host_s = {"launch": 0.0, "retire": 0.0}
         self.phase_s = collections.defaultdict(float)   # host time by phase of _launch
         self.free_streams = list(range(max_inflight))
@@ -218,6 +219,23 @@ class QPServer:
             self.queues[sum(n >= t for t in self.size_classes)].append(req)
             self.cv.notify()
         return fut
+
+    def equalize_staging(self, timeout=10.0):
+        """Grow every stream slot's pinned staging to the largest any slot has needed so far.
+        Slots grow on demand, so after a warm-up only the slots that carried its batches are
+        large; a slot that grows later does so inside a batch's launch (a pinned allocation
+        of tens of MB on the scheduler thread).  Call when no request is pending; it waits
+        (up to `timeout` seconds) for the batches still in flight to retire."""
+        deadline = time.perf_counter() + timeout
+        while True:
+            with self.cv:
+                if not self.inflight and not any(self.queues):
+                    for stg in self.staging:
+                        stg.reserve(*self.stage_peak)
+                    return
+            if time.perf_counter() > deadline:
+                raise RuntimeError("equalize_staging: the server did not become idle")
+            time.sleep(1e-3)
 
     def close(self):
         with self.cv:
@@ -261,6 +279,8 @@ class QPServer:
         isec, n_in = _sections(tin + [(dbytes + esz - 1) // esz])
         osec, n_out = _sections(tout)
         stg.reserve(n_in, n_out, B)
+        self.stage_peak = (max(self.stage_peak[0], n_in), max(self.stage_peak[1], n_out),
+                           max(self.stage_peak[2], B))
         # the descriptors travel in the same staging buffer, after the inputs
         ctypes.memmove(stg.inp.data_ptr() + isec[7] * esz, desc, dbytes)
         src = (ctypes.c_void_p * (7 * B))(*itertools.chain.from_iterable(r.ptrs for r in reqs))

@@ -58,6 +58,10 @@ def test_served_results_equal_alone_match_oracle_and_batches_overlap():
     try:
         futs = [server.submit(*data, g) for data, g in pool]
         results = [f.result(timeout=300) for f in futs]
+        server.equalize_staging()
+        n_in, n_out, nb = server.stage_peak
+        assert n_in > 0 and all(st.inp.numel() >= n_in and st.out.numel() >= n_out
+                                for st in server.staging)
     finally:
         server.close()
     st = server.stats()
