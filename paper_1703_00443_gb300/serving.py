@@ -88,12 +88,23 @@ class Request:
     arrival: float              # time.perf_counter() of arrival
     future: concurrent.futures.Future
     nbytes: int = 0
+    stage_bytes: int = 0        # host staging bytes in its batch (set by submit)
     ptrs: tuple = ()            # host addresses of the six inputs and dl_dz (set by submit)
 
     @property
     def dims(self):
         Q, _, G, _, A, _ = self.data
         return (Q.shape[0], G.shape[0], A.shape[0])
+
+
+def stage_bytes(dims, dtype=torch.float32) -> int:
+    """Host staging bytes one request takes in its batch's pinned buffers: the larger of its
+    packed inputs (with ∂ℓ/∂z*) and its packed results, plus its descriptor."""
+    n, p, m = dims
+    esz = 4 if dtype == torch.float32 else 8
+    r4 = lambda x: (x + 3) // 4 * 4  # noqa: E731
+    data = r4(n * n) + r4(n) + r4(p * n) + r4(p) + r4(m * n) + r4(m)
+    return esz * max(data + r4(n), data + r4(n) + r4(p) + r4(m)) + 128
 
 
 def request_bytes(dims, dtype=torch.float32) -> int:
@@ -107,17 +118,21 @@ def request_bytes(dims, dtype=torch.float32) -> int:
 
 
 class Admission:
-    """Admission policy (host logic only): FIFO, a batch takes requests while the HBM budget
-    and the batch-size cap allow; a request larger than the whole budget is rejected."""
+    """Admission policy (host logic only): FIFO, a batch takes requests while the HBM budget,
+    the batch-size cap and the staging cap allow; a request larger than the whole budget is
+    rejected.  The staging cap bounds a batch's host staging bytes (``stage_bytes`` of its
+    requests) so that it fits the stream slots' preallocated pinned buffers; a batch always
+    takes at least one request."""
 
-    def __init__(self, budget_bytes: int, max_batch: int):
+    def __init__(self, budget_bytes: int, max_batch: int, max_stage_bytes: int | None = None):
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
+        self.max_stage = None if max_stage_bytes is None else int(max_stage_bytes)
         self.reserved = 0
 
     def take(self, queue: collections.deque):
         """Pop the next batch from ``queue``; returns (batch, rejected)."""
-        batch, rejected, total = [], [], 0
+        batch, rejected, total, staged = [], [], 0, 0
         while queue and len(batch) < self.max_batch:
             r = queue[0]
             if r.nbytes > self.budget:
@@ -125,7 +140,11 @@ class Admission:
                 continue
             if self.reserved + total + r.nbytes > self.budget:
                 break
+            sb = getattr(r, "stage_bytes", 0)
+            if batch and self.max_stage is not None and staged + sb > self.max_stage:
+                break
             total += r.nbytes
+            staged += sb
             batch.append(queue.popleft())
         self.reserved += total
         return batch, rejected, total
@@ -175,7 +194,7 @@ class QPServer:
     # [16, 512] (16 stream slots, size classes split at n = 64, 160 and 320, batches of at
     # most 256 requests).
     def __init__(self, device="cuda:0", dtype=torch.float32, max_inflight=16, max_batch=256,
-                 hbm_budget_bytes=8 << 30, options=None, staging_bytes=8 << 20,
+                 hbm_budget_bytes=8 << 30, options=None, staging_bytes=32 << 20,
                  copy_threads=None, size_classes=(64, 160, 320)):
         self.device = torch.device(device)
         self.dtype = dtype
@@ -189,7 +208,10 @@ class QPServer:
         self.host_s = {"launch": 0.0, "retire": 0.0}
         self.phase_s = collections.defaultdict(float)   # host time by phase of _launch
         self.free_streams = list(range(max_inflight))
-        self.admission = Admission(hbm_budget_bytes, max_batch)
+        # batches are capped to the slots' preallocated staging (less room for the per-field
+        # section alignment), so that no slot grows its pinned buffers during a launch
+        self.admission = Admission(hbm_budget_bytes, max_batch,
+                                   max(staging_bytes - (64 << 10), 1 << 20))
         self.size_classes = tuple(sorted(int(t) for t in size_classes))
         self.queues = [collections.deque() for _ in range(len(self.size_classes) + 1)]
         self.cv = threading.Condition()
@@ -213,6 +235,7 @@ class QPServer:
         req = Request(data, np.ascontiguousarray(np.asarray(dl_dz), dtype=npdt),
                       time.perf_counter() if arrival is None else arrival, fut)
         req.nbytes = request_bytes(req.dims, self.dtype)
+        req.stage_bytes = stage_bytes(req.dims, self.dtype)
         req.ptrs = tuple(x.__array_interface__["data"][0] for x in data + (req.dl_dz,))
         with self.cv:
             n = req.dims[0]

@@ -29,6 +29,20 @@ def test_oversized_request_is_rejected_not_blocking():
     assert [r.name for r in b] == [1, 2] and t == 40
 
 
+def test_staging_cap_splits_batches_but_admits_a_large_request_alone():
+    adm = Admission(budget_bytes=1000, max_batch=8, max_stage_bytes=100)
+    q = collections.deque(SimpleNamespace(nbytes=10, stage_bytes=sb, name=i)
+                          for i, sb in enumerate([40, 40, 40, 150, 30]))
+    b1, _, _ = adm.take(q)
+    assert [r.name for r in b1] == [0, 1]            # a third would pass the 100-byte cap
+    b2, _, _ = adm.take(q)
+    assert [r.name for r in b2] == [2]               # the next one is 150 on its own
+    b3, _, _ = adm.take(q)
+    assert [r.name for r in b3] == [3]               # larger than the cap: admitted alone
+    b4, _, _ = adm.take(q)
+    assert [r.name for r in b4] == [4]
+
+
 def test_fifo_order_is_kept_when_head_does_not_fit():
     adm = Admission(budget_bytes=100, max_batch=8)
     adm.reserved = 70
