@@ -121,3 +121,31 @@ def test_sections_are_aligned_and_disjoint():
     assert all(o % 64 == 0 for o in offs)
     ends = [o + max(k, 1) for o, k in zip(offs, [0, 5, 64, 65, 1])]
     assert all(e <= nxt for e, nxt in zip(ends, offs[1:] + [total]))
+
+
+def test_stage_bytes_bound_a_batch_staging():
+    """The admission's staging cap is sound: for batches of mixed sizes, the input and result
+    staging the scheduler lays out (sections per field, each 64-element aligned, plus the
+    descriptors after the inputs) never exceeds the sum of the requests' stage_bytes plus the
+    64 KB margin the server keeps."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1703_00443_gb300 import _lib, inputs
+    from paper_1703_00443_gb300.serving import _sections, stage_bytes
+    lib = _lib.load()
+    for seed in range(5):
+        sizes = inputs.serve_sizes(40, seed=seed, n_hi=256 if seed % 2 else 512)
+        dims = np.array(sizes, dtype=np.int32)
+        B = len(sizes)
+        desc = (_lib.QPInstanceDesc * B)()
+        sz = _lib.QPPackedSizes()
+        assert lib.qp_packed_plan_ex(None, 0, B, dims.ctypes.data_as(ctypes.c_void_p), None, None,
+                                     desc, ctypes.byref(sz)) == 0
+        dbytes = B * ctypes.sizeof(_lib.QPInstanceDesc)
+        _, n_in = _sections([sz.nQ, sz.nq, sz.nG, sz.nh, sz.nA, sz.nb, sz.nq, (dbytes + 3) // 4])
+        _, n_out = _sections([sz.nq, sz.nh, sz.nb, sz.nQ, sz.nq, sz.nG, sz.nh, sz.nA, sz.nb])
+        budget = sum(stage_bytes(s, torch.float32) for s in sizes) + (64 << 10)
+        assert 4 * n_in <= budget and 4 * n_out <= budget
